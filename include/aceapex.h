@@ -1,0 +1,179 @@
+/*
+ * aceapex.h — C ABI of libaceapex.so, a GB300 (sm_103a) decoder for the
+ * absolute-offset LZ77 block format of "Compressed-Resident Genomics:
+ * Full-Pipeline Device-Resident GPU LZ77 Decode with Position-Invariant
+ * Random Access" (arXiv 2606.18900). The byte format is frozen in FORMAT.md.
+ *
+ * Conventions
+ *  - Every function returns an aceapex_status (0 = ACEAPEX_OK) unless noted.
+ *  - Pointers named d_* are device pointers on the archive's device; h_*
+ *    are host pointers. Sizes are bytes. Positions are absolute byte offsets
+ *    into the decompressed output.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Decode calls are stream-ordered and asynchronous: the returned
+ *    status covers argument and host-side validation only. Errors found by
+ *    the kernels (a corrupt segment, a dependency wait that ran out of time)
+ *    are latched in a device error word and reported by aceapex_last_error.
+ *  - The library never writes outside [d_out, d_out + out_cap).
+ *  - Calls on one archive handle must be serialised by the caller (one
+ *    host thread at a time, and stream-ordered or synchronised between
+ *    calls that use different streams): a handle owns one set of work
+ *    counters, flags and scratch.
+ */
+#ifndef ACEAPEX_H
+#define ACEAPEX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ACEAPEX_OK = 0,
+  ACEAPEX_EINVAL = 1,   /* bad argument */
+  ACEAPEX_ECORRUPT = 2, /* archive breaks a rule of FORMAT.md */
+  ACEAPEX_ENOMEM = 3,   /* host or device allocation failed, or over budget */
+  ACEAPEX_ECUDA = 4,    /* a CUDA runtime call failed */
+  ACEAPEX_ETIMEOUT = 5, /* a dependency wait ran past its time limit */
+  ACEAPEX_ERANGE = 6,   /* position or size outside the archive / buffer */
+  ACEAPEX_EBUSY = 7     /* admission refused (serving) */
+} aceapex_status;
+
+typedef struct aceapex_archive aceapex_archive;
+
+/* Static per-archive byte counts (from the segment directory; no decode). */
+typedef struct {
+  uint64_t decoded_bytes;    /* U: N, bytes written by a full decode */
+  uint64_t compressed_bytes; /* C: payload + directory + tables read by a full decode */
+  uint64_t match_bytes;      /* M: sum of match lengths (match-source bytes read) */
+  uint64_t literal_bytes;    /* literal bytes (N - M) */
+  uint64_t n_commands;       /* matches in the archive */
+  uint64_t n_segments;       /* 16 KiB (or smaller) decode units */
+  uint64_t n_blocks;         /* B-byte blocks (paper's block size) */
+  uint64_t n_deps;           /* dependency-list entries */
+  uint64_t n_reads;          /* read-index entries */
+  uint32_t max_level;        /* deepest level present */
+  uint32_t log2_B, log2_S, W;
+} aceapex_stats;
+
+/*
+ * Open an archive: validate it on the host (FORMAT.md §6) and copy the
+ * sections the decoder needs into device memory on `device` (paper §3.3:
+ * the archive is resident in VRAM before decoding; the copy is outside any
+ * decode timer). The host bytes are not retained. On success *out owns the
+ * device copies, flags, work counters and scratch; free it with
+ * aceapex_close. Errors: EINVAL (null/zero arguments), ECORRUPT, ENOMEM,
+ * ECUDA.
+ */
+int aceapex_open(const void *h_archive, uint64_t nbytes, int device, aceapex_archive **out);
+
+/* Release every device and host resource of the handle (NULL is a no-op).
+ * Synchronises the device first so that no kernel still uses them. */
+void aceapex_close(aceapex_archive *a);
+
+/* Decompressed size N of the archive (0 for NULL). */
+uint64_t aceapex_decoded_size(const aceapex_archive *a);
+
+/* Fill *st with the archive's static counts. */
+int aceapex_get_stats(const aceapex_archive *a, aceapex_stats *st);
+
+/*
+ * Whole-file device-resident decode (paper §3.3, "v4": entropy decode and
+ * match resolution both on the GPU, output kept in VRAM). Writes the N
+ * decoded bytes to d_out[0..N). One persistent launch: each warp takes the
+ * next segment in level order, rANS-decodes its four streams, waits for the
+ * segments its matches read (bounded wait), resolves its commands and
+ * publishes its ready flag. Errors: EINVAL, ERANGE (out_cap < N), ECUDA.
+ * opt_stats, when not NULL, receives aceapex_get_stats.
+ */
+int aceapex_decode_all(aceapex_archive *a, void *d_out, uint64_t out_cap, void *stream, aceapex_stats *opt_stats);
+
+/*
+ * Range decode (paper §4, "v7-RA"): write exactly the bytes [byte_lo,
+ * byte_hi) of the decompressed output to d_out[0 .. byte_hi - byte_lo).
+ * Decodes only the covering segments and their transitive source closure
+ * (from the stored dependency lists) into the handle's scratch arena, then
+ * gathers the requested bytes. Errors: EINVAL, ERANGE (hi > N, lo > hi,
+ * out_cap too small), ENOMEM, ECUDA.
+ */
+int aceapex_decode_range(aceapex_archive *a, uint64_t byte_lo, uint64_t byte_hi, void *d_out, uint64_t out_cap,
+                         void *stream);
+
+/*
+ * Read-to-block index lookup (paper §4.1): record `read_id` (0-based) covers
+ * [*byte_lo, *byte_hi). Host only, O(1), no GPU work. Errors: EINVAL (no
+ * index or NULL pointers), ERANGE (read_id >= n_reads).
+ */
+int aceapex_read_lookup(const aceapex_archive *a, uint64_t read_id, uint64_t *byte_lo, uint64_t *byte_hi);
+
+/*
+ * Report the device error word of the handle and clear it. sync != 0 first
+ * synchronises `stream` (or the device when stream is NULL) so the word
+ * covers every call issued before. Returns ACEAPEX_OK, ECORRUPT, ETIMEOUT or
+ * ECUDA.
+ */
+int aceapex_last_error(aceapex_archive *a, int sync, void *stream);
+
+/*
+ * Set the time limit of every dependency wait of later launches, in
+ * nanoseconds (default 2e9). A wait that reaches the limit latches ETIMEOUT
+ * and the launch finishes without hanging. 0 restores the default.
+ */
+int aceapex_set_wait_limit(aceapex_archive *a, uint64_t ns);
+
+/*
+ * Test hook: segments whose index is in h_segs[0..n) never publish their
+ * ready flag in later launches (n = 0 clears the list). Dependent segments
+ * then run into the wait limit. Lets the tests exercise ETIMEOUT without
+ * faulting or hanging a GPU.
+ */
+int aceapex_debug_block_segments(aceapex_archive *a, const uint32_t *h_segs, uint32_t n);
+
+/*
+ * Streaming range decode through a fixed device ring (paper §5: output size
+ * decoupled from device memory). Decodes [byte_lo, byte_hi) window by
+ * window; window k covers [byte_lo + k*window_bytes, min(byte_hi, byte_lo +
+ * (k+1)*window_bytes)) and its CRC-32 (IEEE, zlib polynomial; replaces the
+ * paper's FNV check) is written to d_crc_per_window[k] on the device. Needs
+ * an archive with a distance bound D and ring_bytes >= window_bytes + D +
+ * 2*S rounded up to a power of two; window_bytes must be a multiple of the
+ * segment size. The ring is owned by the handle (allocated on first use).
+ * Errors: EINVAL (D == 0, bad sizes), ERANGE, ENOMEM, ECUDA.
+ */
+int aceapex_stream_range(aceapex_archive *a, uint64_t byte_lo, uint64_t byte_hi, uint64_t ring_bytes,
+                         uint64_t window_bytes, uint32_t *d_crc_per_window, void *stream);
+
+/*
+ * Batched decode of n archives into n caller buffers (d_outs[i] holds at
+ * least aceapex_decoded_size(as[i]) bytes) in one persistent launch; the
+ * work list interleaves the archives' segments in level order. All archives
+ * must live on the same device. Errors: EINVAL, ECUDA, ENOMEM.
+ */
+int aceapex_decode_batch(aceapex_archive *const *as, int n, void *const *d_outs, void *stream);
+
+/*
+ * Host encoder (paper §2: global match search, absolute offsets, fixed
+ * blocks; the paper's encoder is CPU-only too). Produces a FORMAT.md v1
+ * archive of h_in[0..n) in a malloc'd buffer *h_out (*out_len bytes; free
+ * with aceapex_free). log2_B: block size exponent (2..30); min_match: 0 =
+ * 4 + W; max_level: level cap; dist_bound: 0 = unbounded; h_reads /
+ * n_reads: optional read index (record start offsets); threads: 0 = all
+ * cores. Deterministic for any thread count. Errors: EINVAL, ENOMEM.
+ */
+int aceapex_encode(const void *h_in, uint64_t n, uint32_t log2_B, uint32_t min_match, uint32_t max_level,
+                   uint64_t dist_bound, const uint64_t *h_reads, uint64_t n_reads, int threads, void **h_out,
+                   uint64_t *out_len);
+
+/* Free a buffer returned by aceapex_encode. */
+void aceapex_free(void *p);
+
+/* FASTQ record start offsets of h_in (every fourth line starts a record);
+ * writes at most cap entries to h_out and returns the total count. */
+uint64_t aceapex_fastq_index(const void *h_in, uint64_t n, uint64_t *h_out, uint64_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACEAPEX_H */

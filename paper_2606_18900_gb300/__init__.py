@@ -1,0 +1,273 @@
+"""GB300-native device-resident decoder for the absolute-offset LZ77 block
+format of arXiv 2606.18900 ("Compressed-Resident Genomics").
+
+This module is a thin ctypes binding over ``libaceapex.so`` (C ABI in
+``include/aceapex.h``): it marshals arguments and nothing else. Every step of
+the decode path runs in the library's CUDA kernels; PyTorch only provides
+device memory and streams. There is no CPU fallback: when the library is
+missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_CSRC = os.path.join(_HERE, "csrc")
+_SO = os.path.join(_HERE, "libaceapex.so")
+_INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
+_SOURCES = ["kernels.cu", "host.cpp", "encoder.cpp"]
+_lock = threading.Lock()
+_lib = None
+
+OK, EINVAL, ECORRUPT, ENOMEM, ECUDA, ETIMEOUT, ERANGE, EBUSY = range(8)
+STATUS = {0: "OK", 1: "EINVAL", 2: "ECORRUPT", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT", 6: "ERANGE", 7: "EBUSY"}
+
+ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+
+
+class AceapexError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+def _nvcc() -> str:
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if c and (os.path.isabs(c) and os.path.exists(c) or not os.path.isabs(c)):
+            return c
+    return "nvcc"
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libaceapex.so in-tree for sm_103a (three translation units in
+    parallel, then one link)."""
+    srcs = [os.path.join(_CSRC, s) for s in _SOURCES]
+    deps = srcs + [os.path.join(_CSRC, h) for h in ("format.h", "kernels.h")] + [os.path.join(_INCLUDE, "aceapex.h")]
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(os.path.getmtime(d) for d in deps):
+        return _SO
+    nvcc = _nvcc()
+    bdir = os.path.join(_HERE, "_build")
+    os.makedirs(bdir, exist_ok=True)
+    common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + _CSRC, "-I" + _INCLUDE]
+
+    def compile_one(src):
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
+        cmd = [nvcc, "-c", src, "-o", obj] + common
+        if src.endswith(".cu"):
+            cmd += [ARCH, "-lineinfo", "-Xptxas", "-v" if verbose else "-O3"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
+        if verbose:
+            print(r.stderr)
+        return obj
+
+    with ThreadPoolExecutor(len(srcs)) as ex:
+        objs = list(ex.map(compile_one, srcs))
+    tmp = _SO + f".tmp{os.getpid()}"
+    r = subprocess.run([nvcc, "-shared", ARCH, "-o", tmp] + objs + ["-lpthread"], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stderr}")
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("decoded_bytes", "compressed_bytes", "match_bytes", "literal_bytes",
+                                               "n_commands", "n_segments", "n_blocks", "n_deps", "n_reads")] + \
+               [(k, ctypes.c_uint32) for k in ("max_level", "log2_B", "log2_S", "W")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def lib():
+    """The loaded library (built first when out of date)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_SO):
+                build()
+            L = ctypes.CDLL(_SO)
+            vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+            u64p = ctypes.POINTER(ctypes.c_uint64)
+            L.aceapex_open.argtypes = [vp, u64, i32, ctypes.POINTER(vp)]
+            L.aceapex_close.argtypes = [vp]
+            L.aceapex_close.restype = None
+            L.aceapex_decoded_size.argtypes = [vp]
+            L.aceapex_decoded_size.restype = u64
+            L.aceapex_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+            L.aceapex_decode_all.argtypes = [vp, vp, u64, vp, ctypes.POINTER(Stats)]
+            L.aceapex_decode_range.argtypes = [vp, u64, u64, vp, u64, vp]
+            L.aceapex_read_lookup.argtypes = [vp, u64, u64p, u64p]
+            L.aceapex_last_error.argtypes = [vp, i32, vp]
+            L.aceapex_set_wait_limit.argtypes = [vp, u64]
+            L.aceapex_debug_block_segments.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), u32]
+            L.aceapex_stream_range.argtypes = [vp, u64, u64, u64, u64, vp, vp]
+            L.aceapex_decode_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), vp]
+            L.aceapex_encode.argtypes = [vp, u64, u32, u32, u32, u64, u64p, u64, i32, ctypes.POINTER(vp), u64p]
+            L.aceapex_free.argtypes = [vp]
+            L.aceapex_free.restype = None
+            L.aceapex_fastq_index.argtypes = [vp, u64, u64p, u64]
+            L.aceapex_fastq_index.restype = u64
+            for f in ("aceapex_open", "aceapex_get_stats", "aceapex_decode_all", "aceapex_decode_range",
+                      "aceapex_read_lookup", "aceapex_last_error", "aceapex_set_wait_limit",
+                      "aceapex_debug_block_segments", "aceapex_stream_range", "aceapex_decode_batch",
+                      "aceapex_encode"):
+                getattr(L, f).restype = i32
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise AceapexError(rc, what)
+
+
+def _ptr(x) -> int:
+    """Device or host address of a torch tensor / numpy array / int."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s) -> int:
+    if s is None:
+        return 0
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream  # torch.cuda.Stream
+
+
+def _as_u8(data) -> np.ndarray:
+    if isinstance(data, np.ndarray):
+        return np.ascontiguousarray(data.reshape(-1).view(np.uint8))
+    return np.frombuffer(bytes(data), dtype=np.uint8)
+
+
+# -------------------------------------------------------------------- host API
+
+def encode(data, log2_B: int = 14, min_match: int = 0, max_level: int = 8, dist_bound: int = 0,
+           reads=None, threads: int = 0) -> np.ndarray:
+    """Host encoder of the library: returns the archive bytes (uint8 array)."""
+    L = lib()
+    buf = _as_u8(data)
+    r = np.ascontiguousarray(reads if reads is not None else np.empty(0), dtype=np.uint64)
+    out = ctypes.c_void_p()
+    n = ctypes.c_uint64()
+    rc = L.aceapex_encode(buf.ctypes.data if buf.size else None, buf.size, log2_B, min_match, max_level, dist_bound,
+                          r.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) if r.size else None, r.size, threads,
+                          ctypes.byref(out), ctypes.byref(n))
+    _check(rc, "aceapex_encode")
+    arr = np.empty(n.value, dtype=np.uint8)
+    ctypes.memmove(arr.ctypes.data, out.value, n.value)
+    L.aceapex_free(out)
+    return arr
+
+
+def fastq_index(data) -> np.ndarray:
+    L = lib()
+    buf = _as_u8(data)
+    n = L.aceapex_fastq_index(buf.ctypes.data, buf.size, None, 0)
+    out = np.zeros(max(n, 1), dtype=np.uint64)
+    L.aceapex_fastq_index(buf.ctypes.data, buf.size, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), n)
+    return out[:n]
+
+
+# ------------------------------------------------------------------- archives
+
+class Archive:
+    """A device-resident archive (aceapex_open / aceapex_close)."""
+
+    def __init__(self, archive_bytes, device: int = 0):
+        L = lib()
+        buf = _as_u8(archive_bytes)
+        h = ctypes.c_void_p()
+        _check(L.aceapex_open(buf.ctypes.data, buf.size, device, ctypes.byref(h)), "aceapex_open")
+        self._h = h
+        self.device = device
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().aceapex_close(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def size(self) -> int:
+        return int(lib().aceapex_decoded_size(self._h))
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(lib().aceapex_get_stats(self._h, ctypes.byref(st)), "aceapex_get_stats")
+        return st.as_dict()
+
+    def decode_all(self, out, stream=None):
+        """Decode the whole archive into device buffer ``out`` (async)."""
+        cap = out.numel() * out.element_size() if hasattr(out, "numel") else int(out[1])
+        _check(lib().aceapex_decode_all(self._h, _ptr(out if hasattr(out, "numel") else out[0]), cap,
+                                        _stream(stream), None), "aceapex_decode_all")
+
+    def decode_range(self, lo: int, hi: int, out, stream=None):
+        cap = out.numel() * out.element_size()
+        _check(lib().aceapex_decode_range(self._h, lo, hi, _ptr(out), cap, _stream(stream)), "aceapex_decode_range")
+
+    def read_lookup(self, read_id: int):
+        lo, hi = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().aceapex_read_lookup(self._h, read_id, ctypes.byref(lo), ctypes.byref(hi)), "aceapex_read_lookup")
+        return lo.value, hi.value
+
+    def stream_range(self, lo: int, hi: int, ring_bytes: int, window: int, crc_out, stream=None):
+        _check(lib().aceapex_stream_range(self._h, lo, hi, ring_bytes, window, _ptr(crc_out), _stream(stream)),
+               "aceapex_stream_range")
+
+    def last_error(self, sync: bool = True, stream=None) -> int:
+        return int(lib().aceapex_last_error(self._h, int(sync), _stream(stream)))
+
+    def check(self, stream=None):
+        """Synchronise and raise if a kernel latched an error."""
+        _check(self.last_error(True, stream), "device error")
+
+    def set_wait_limit(self, ns: int):
+        _check(lib().aceapex_set_wait_limit(self._h, ns), "aceapex_set_wait_limit")
+
+    def debug_block_segments(self, segs):
+        a = np.ascontiguousarray(segs, dtype=np.uint32)
+        _check(lib().aceapex_debug_block_segments(
+            self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)) if a.size else None, a.size),
+            "aceapex_debug_block_segments")
+
+
+def decode_batch(archives, outs, stream=None):
+    """One persistent launch over several archives (aceapex_decode_batch)."""
+    n = len(archives)
+    hs = (ctypes.c_void_p * n)(*[a.handle for a in archives])
+    ps = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
+    _check(lib().aceapex_decode_batch(hs, n, ps, _stream(stream)), "aceapex_decode_batch")

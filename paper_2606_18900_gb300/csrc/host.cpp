@@ -1,0 +1,720 @@
+// Host side of libaceapex.so: archive validation (FORMAT.md §6), device
+// residency (paper §3.3), work lists in level order, source closures for range
+// decode (paper §4), the ring streamer (paper §5), batching, and the C ABI
+// declared in include/aceapex.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/aceapex.h"
+#include "format.h"
+#include "kernels.h"
+
+namespace aceapex {
+int encode_archive(const uint8_t *in, uint64_t n, uint32_t log2_B, uint32_t min_match, uint32_t cap, uint64_t D,
+                   const uint64_t *reads, uint64_t n_reads, int threads, uint8_t **out, uint64_t *out_len);
+uint64_t fastq_index(const uint8_t *in, uint64_t n, uint64_t *out, uint64_t cap);
+}  // namespace aceapex
+
+using namespace aceapex;
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;
+
+template <class T>
+T rd(const uint8_t *p) {
+  T v;
+  std::memcpy(&v, p, sizeof(T));
+  return v;
+}
+
+// One library-wide epoch counter per device: epochs never repeat on a device,
+// so a ready flag can never be mistaken for one of another call.
+struct DeviceState {
+  uint32_t *d_global_epoch = nullptr;
+};
+std::mutex g_dev_mu;
+std::map<int, DeviceState> g_dev;
+
+uint32_t *global_epoch(int device) {
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  DeviceState &d = g_dev[device];
+  if (!d.d_global_epoch) {
+    if (cudaMalloc(&d.d_global_epoch, sizeof(uint32_t)) != cudaSuccess) return nullptr;
+    if (cudaMemset(d.d_global_epoch, 0, sizeof(uint32_t)) != cudaSuccess) return nullptr;
+  }
+  return d.d_global_epoch;
+}
+
+// device buffer that owns its memory
+template <class T>
+struct DBuf {
+  T *p = nullptr;
+  uint64_t n = 0;
+  cudaError_t alloc(uint64_t count) {
+    release();
+    n = count;
+    if (!count) return cudaSuccess;
+    return cudaMalloc(&p, count * sizeof(T));
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+// pinned host staging whose previous async copy is waited for before reuse
+struct Staging {
+  void *p = nullptr;
+  uint64_t bytes = 0;
+  cudaEvent_t done = nullptr;
+  bool pending = false;
+  cudaError_t reserve(uint64_t b) {
+    if (pending) cudaEventSynchronize(done), pending = false;
+    if (b <= bytes) return cudaSuccess;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMallocHost(&p, b);
+    if (e == cudaSuccess) bytes = b;
+    if (!done) cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    return e;
+  }
+  void mark(cudaStream_t st) {
+    cudaEventRecord(done, st);
+    pending = true;
+  }
+  void release() {
+    if (pending) cudaEventSynchronize(done);
+    if (p) cudaFreeHost(p);
+    if (done) cudaEventDestroy(done);
+    p = nullptr;
+    done = nullptr;
+    bytes = 0;
+    pending = false;
+  }
+};
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? ACEAPEX_OK : ACEAPEX_ECUDA; }
+
+}  // namespace
+
+struct aceapex_archive {
+  int device = 0;
+  Header h{};
+  std::vector<SegRec> dir;
+  std::vector<uint64_t> dep_ptr;
+  std::vector<uint32_t> deps;
+  std::vector<uint64_t> reads;
+  aceapex_stats stats{};
+
+  DBuf<uint8_t> d_payload;
+  DBuf<SegRec> d_dir;
+  DBuf<uint32_t> d_lut;
+  DBuf<uint32_t> d_flags;
+  DBuf<WorkItem> d_order;    // all segments in level order
+  DBuf<uint32_t> d_words;    // [0] err, [1] epoch, [2] counter
+  DBuf<uint8_t> d_blocked;
+  DBuf<uint8_t> d_scratch;
+  uint32_t scratch_warps = 0;
+  int grid = 0;
+  uint64_t wait_ns = kDefaultWaitNs;
+  bool any_blocked = false;
+
+  // range decode: page table, arena of slots, work list
+  DBuf<uint32_t> d_page;
+  DBuf<uint8_t> d_arena;
+  DBuf<WorkItem> d_work;
+  Staging stage_work;
+  std::vector<uint32_t> mark;
+  uint32_t mark_gen = 0;
+
+  // ring streaming
+  DBuf<uint8_t> d_ring;
+  DBuf<uint32_t> d_seg_crc;
+  // batch
+  DBuf<DevArchive> d_batch_arcs;
+  DBuf<OutView> d_batch_views;
+  DBuf<WorkItem> d_batch_work;
+  Staging stage_batch;
+
+  uint32_t *err() const { return d_words.p; }
+  uint32_t *epoch() const { return d_words.p + 1; }
+  uint32_t *counter() const { return d_words.p + 2; }
+
+  DevArchive dev() const {
+    DevArchive A{};
+    A.payload = d_payload.p;
+    A.dir = d_dir.p;
+    A.dep_ptr = nullptr;
+    A.deps = nullptr;
+    A.lut = d_lut.p;
+    A.flags = d_flags.p;
+    A.blocked = any_blocked ? d_blocked.p : nullptr;
+    A.n = h.n;
+    A.D = h.D;
+    A.log2_S = h.log2_S;
+    A.W = h.W;
+    A.min_match = h.min_match;
+    A.n_seg = (uint32_t)h.n_seg;
+    return A;
+  }
+
+  void release() {
+    d_payload.release(); d_dir.release(); d_lut.release(); d_flags.release(); d_order.release();
+    d_words.release(); d_blocked.release(); d_scratch.release(); d_page.release(); d_arena.release();
+    d_work.release(); d_ring.release(); d_seg_crc.release(); d_batch_arcs.release(); d_batch_views.release();
+    d_batch_work.release();
+    stage_work.release();
+    stage_batch.release();
+  }
+};
+
+namespace {
+
+// FORMAT.md §6 host-side checks; fills h, dir, dep_ptr, deps, reads, stats.
+int validate(const uint8_t *a, uint64_t len, aceapex_archive *A) {
+  if (len < kHeaderBytes + kTablesBytes || std::memcmp(a, "ACEAPEX1", 8) != 0) return ACEAPEX_ECORRUPT;
+  if (rd<uint32_t>(a + 8) != 1 || rd<uint32_t>(a + 12) != kHeaderBytes) return ACEAPEX_ECORRUPT;
+  Header &h = A->h;
+  h.n = rd<uint64_t>(a + 16);
+  h.log2_B = a[24];
+  h.log2_S = a[25];
+  h.W = a[26];
+  h.min_match = a[27];
+  h.max_level = a[30];
+  h.flags = a[31];
+  if (a[28] != kScaleBits || a[29] != kLanes || (h.flags & ~1u)) return ACEAPEX_ECORRUPT;
+  if (h.log2_B < 2 || h.log2_B > 30 || h.log2_S != std::min<uint32_t>(h.log2_B, kMaxLog2S)) return ACEAPEX_ECORRUPT;
+  if (h.W != offset_width(h.n) || h.min_match < 1) return ACEAPEX_ECORRUPT;
+  h.D = rd<uint64_t>(a + 32);
+  h.n_seg = rd<uint64_t>(a + 40);
+  h.n_deps = rd<uint64_t>(a + 48);
+  h.n_reads = rd<uint64_t>(a + 56);
+  const uint64_t S = uint64_t(1) << h.log2_S;
+  if (h.n_seg != (h.n + S - 1) / S || h.n_seg >= (uint64_t(1) << 32)) return ACEAPEX_ECORRUPT;
+  if (!(h.flags & 1) && h.n_reads) return ACEAPEX_ECORRUPT;
+  if (h.n_seg > len / 24 || h.n_deps > len / 4 || h.n_reads > len / 8) return ACEAPEX_ECORRUPT;
+  h.off_tables = rd<uint64_t>(a + 64);
+  h.off_dir = rd<uint64_t>(a + 72);
+  h.off_dep_ptr = rd<uint64_t>(a + 80);
+  h.off_deps = rd<uint64_t>(a + 88);
+  h.off_reads = rd<uint64_t>(a + 96);
+  h.off_payload = rd<uint64_t>(a + 104);
+  h.payload_bytes = rd<uint64_t>(a + 112);
+  h.total_bytes = rd<uint64_t>(a + 120);
+  if (h.off_tables != kHeaderBytes || h.off_dir != kHeaderBytes + kTablesBytes ||
+      h.off_dep_ptr != round16(h.off_dir + 24 * h.n_seg) ||
+      h.off_deps != round16(h.off_dep_ptr + 8 * (h.n_seg + 1)) ||
+      h.off_reads != round16(h.off_deps + 4 * h.n_deps) || h.off_payload != round16(h.off_reads + 8 * h.n_reads) ||
+      h.total_bytes != h.off_payload + h.payload_bytes || h.total_bytes != len)
+    return ACEAPEX_ECORRUPT;
+  // tables
+  for (int c = 0; c < 4; ++c) {
+    uint32_t sum = 0;
+    for (int s = 0; s < 256; ++s) sum += rd<uint16_t>(a + kHeaderBytes + 512 * c + 2 * s);
+    if (sum != 0 && sum != kScale) return ACEAPEX_ECORRUPT;
+  }
+  // directory
+  A->dir.resize(h.n_seg);
+  if (h.n_seg) std::memcpy(A->dir.data(), a + h.off_dir, 24 * h.n_seg);
+  uint64_t po = 0, n_lit = 0, n_cmd = 0;
+  uint32_t max_lv = 0;
+  for (uint64_t s = 0; s < h.n_seg; ++s) {
+    const SegRec &r = A->dir[s];
+    if (r.payload_off != po || r.zero != 0) return ACEAPEX_ECORRUPT;
+    if ((uint64_t)r.n_cmd * (4 + h.W) + r.n_lit > kMaxSym) return ACEAPEX_ECORRUPT;
+    if (r.level > h.max_level) return ACEAPEX_ECORRUPT;
+    const uint64_t out_size = std::min<uint64_t>(S, h.n - s * S);
+    if (r.n_lit > out_size || (uint64_t)r.n_cmd * h.min_match > out_size - r.n_lit) return ACEAPEX_ECORRUPT;
+    po = round16(po + 128 + 2 * (uint64_t)r.n_words);
+    n_lit += r.n_lit;
+    n_cmd += r.n_cmd;
+    max_lv = std::max<uint32_t>(max_lv, r.level);
+  }
+  if (po != h.payload_bytes) return ACEAPEX_ECORRUPT;
+  // dependency lists, ascending, below their segment, level consistent
+  A->dep_ptr.resize(h.n_seg + 1);
+  std::memcpy(A->dep_ptr.data(), a + h.off_dep_ptr, 8 * (h.n_seg + 1));
+  A->deps.resize(h.n_deps);
+  if (h.n_deps) std::memcpy(A->deps.data(), a + h.off_deps, 4 * h.n_deps);
+  if (A->dep_ptr[0] != 0 || A->dep_ptr[h.n_seg] != h.n_deps) return ACEAPEX_ECORRUPT;
+  for (uint64_t s = 0; s < h.n_seg; ++s) {
+    uint64_t b = A->dep_ptr[s], e = A->dep_ptr[s + 1];
+    if (e < b || e > h.n_deps) return ACEAPEX_ECORRUPT;
+    uint32_t lv = 0;
+    for (uint64_t i = b; i < e; ++i) {
+      uint32_t d = A->deps[i];
+      if (d >= s || (i > b && d <= A->deps[i - 1])) return ACEAPEX_ECORRUPT;
+      lv = std::max<uint32_t>(lv, A->dir[d].level + 1u);
+    }
+    if (lv != A->dir[s].level) return ACEAPEX_ECORRUPT;
+  }
+  // read index
+  A->reads.resize(h.n_reads);
+  if (h.n_reads) std::memcpy(A->reads.data(), a + h.off_reads, 8 * h.n_reads);
+  for (uint64_t r = 0; r < h.n_reads; ++r)
+    if (A->reads[r] >= h.n || (r && A->reads[r] <= A->reads[r - 1])) return ACEAPEX_ECORRUPT;
+
+  aceapex_stats &st = A->stats;
+  st.decoded_bytes = h.n;
+  st.compressed_bytes = h.payload_bytes + 24 * h.n_seg + kTablesBytes;
+  st.literal_bytes = n_lit;
+  st.match_bytes = h.n - n_lit;
+  st.n_commands = n_cmd;
+  st.n_segments = h.n_seg;
+  st.n_blocks = (h.n + (uint64_t(1) << h.log2_B) - 1) >> h.log2_B;
+  st.n_deps = h.n_deps;
+  st.n_reads = h.n_reads;
+  st.max_level = max_lv;
+  st.log2_B = h.log2_B;
+  st.log2_S = h.log2_S;
+  st.W = h.W;
+  return ACEAPEX_OK;
+}
+
+// decode table: slot -> sym | (slot - cum) << 8 | (freq - 1) << 20
+void build_lut(const uint8_t *a, std::vector<uint32_t> &lut) {
+  lut.assign(4 * kScale, 0);
+  for (int c = 0; c < 4; ++c) {
+    uint32_t cum = 0;
+    for (int s = 0; s < 256; ++s) {
+      uint32_t f = rd<uint16_t>(a + kHeaderBytes + 512 * c + 2 * s);
+      for (uint32_t k = 0; k < f; ++k) lut[c * kScale + cum + k] = (uint32_t)s | (k << 8) | ((f - 1) << 20);
+      cum += f;
+    }
+  }
+}
+
+// segments sorted by (level, index)
+void level_order(const std::vector<SegRec> &dir, const uint32_t *segs, uint64_t n, uint32_t arc,
+                 std::vector<WorkItem> &out) {
+  uint32_t cnt[257] = {};
+  for (uint64_t i = 0; i < n; ++i) cnt[dir[segs ? segs[i] : i].level + 1]++;
+  for (int l = 0; l < 256; ++l) cnt[l + 1] += cnt[l];
+  size_t base = out.size();
+  out.resize(base + n);
+  for (uint64_t i = 0; i < n; ++i) {
+    uint32_t s = segs ? segs[i] : (uint32_t)i;
+    out[base + cnt[dir[s].level]++] = WorkItem{arc, s};
+  }
+}
+
+int ensure_scratch(aceapex_archive *A) {
+  if (A->d_scratch.p) return ACEAPEX_OK;
+  A->grid = decode_grid(A->device, kBlock);
+  A->scratch_warps = (uint32_t)A->grid * (kBlock / 32);
+  if (A->d_scratch.alloc((uint64_t)A->scratch_warps * kStageBytes) != cudaSuccess) return ACEAPEX_ENOMEM;
+  return ACEAPEX_OK;
+}
+
+DecodeLaunch base_launch(aceapex_archive *A) {
+  DecodeLaunch L{};
+  L.arc0 = A->dev();
+  L.epoch = A->epoch();
+  L.counter = A->counter();
+  L.err = A->err();
+  L.scratch = A->d_scratch.p;
+  L.scratch_warps = A->scratch_warps;
+  L.wait_ns = A->wait_ns;
+  return L;
+}
+
+OutView linear_view(uint8_t *base, uint64_t origin) {
+  OutView v{};
+  v.base = base;
+  v.origin = origin;
+  v.mask = ~uint64_t(0);
+  return v;
+}
+
+// transitive source closure of segments [s_lo, s_hi] (host, from the stored lists)
+void closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, std::vector<uint32_t> &out) {
+  if (A->mark.size() != A->h.n_seg) A->mark.assign(A->h.n_seg, 0);
+  if (++A->mark_gen == 0) {
+    std::fill(A->mark.begin(), A->mark.end(), 0);
+    A->mark_gen = 1;
+  }
+  const uint32_t g = A->mark_gen;
+  out.clear();
+  std::vector<uint32_t> stack;
+  for (uint64_t s = s_lo; s <= s_hi; ++s)
+    if (A->mark[s] != g) {
+      A->mark[s] = g;
+      stack.push_back((uint32_t)s);
+    }
+  while (!stack.empty()) {
+    uint32_t s = stack.back();
+    stack.pop_back();
+    out.push_back(s);
+    for (uint64_t i = A->dep_ptr[s]; i < A->dep_ptr[s + 1]; ++i) {
+      uint32_t d = A->deps[i];
+      if (A->mark[d] != g) {
+        A->mark[d] = g;
+        stack.push_back(d);
+      }
+    }
+  }
+}
+
+// decode the closure of [s_lo, s_hi] into arena slots (paged view); returns the view
+int decode_closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, cudaStream_t st, OutView *view_out,
+                   uint32_t *n_out, bool begin) {
+  std::vector<uint32_t> segs;
+  closure(A, s_lo, s_hi, segs);
+  std::vector<WorkItem> work;
+  level_order(A->dir, segs.data(), segs.size(), 0, work);
+  const uint64_t S = uint64_t(1) << A->h.log2_S;
+  if (!A->d_page.p) {
+    if (A->d_page.alloc(A->h.n_seg) != cudaSuccess) return ACEAPEX_ENOMEM;
+    if (cudaMemsetAsync(A->d_page.p, 0xFF, 4 * A->h.n_seg, st) != cudaSuccess) return ACEAPEX_ECUDA;
+  }
+  if (A->d_arena.n < work.size() * S) {
+    cudaStreamSynchronize(st);
+    uint64_t slots = std::max<uint64_t>(work.size(), 64);
+    if (A->d_arena.alloc(slots * S) != cudaSuccess) return ACEAPEX_ENOMEM;
+  }
+  if (A->d_work.n < work.size()) {
+    cudaStreamSynchronize(st);
+    if (A->d_work.alloc(std::max<uint64_t>(work.size(), 1024)) != cudaSuccess) return ACEAPEX_ENOMEM;
+  }
+  if (A->stage_work.reserve(work.size() * sizeof(WorkItem)) != cudaSuccess) return ACEAPEX_ENOMEM;
+  std::memcpy(A->stage_work.p, work.data(), work.size() * sizeof(WorkItem));
+  cudaError_t e = cudaMemcpyAsync(A->d_work.p, A->stage_work.p, work.size() * sizeof(WorkItem),
+                                  cudaMemcpyHostToDevice, st);
+  A->stage_work.mark(st);
+  if (e != cudaSuccess) return ACEAPEX_ECUDA;
+  if ((e = launch_set_pages(A->d_page.p, A->d_work.p, (uint32_t)work.size(), st)) != cudaSuccess) return ACEAPEX_ECUDA;
+  uint32_t *ge = global_epoch(A->device);
+  if (!ge) return ACEAPEX_ECUDA;
+  if (begin && (e = launch_begin(ge, A->epoch(), A->counter(), st)) != cudaSuccess) return ACEAPEX_ECUDA;
+  if (!begin && (e = cudaMemsetAsync(A->counter(), 0, 4, st)) != cudaSuccess) return ACEAPEX_ECUDA;
+  DecodeLaunch L = base_launch(A);
+  OutView v{};
+  v.page = A->d_page.p;
+  v.slot_base = A->d_arena.p;
+  L.view0 = v;
+  L.work = A->d_work.p;
+  L.n_work = (uint32_t)work.size();
+  if ((e = launch_decode(L, A->grid, kBlock, st)) != cudaSuccess) return ACEAPEX_ECUDA;
+  *view_out = v;
+  *n_out = (uint32_t)work.size();
+  return ACEAPEX_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+int aceapex_open(const void *h_archive, uint64_t nbytes, int device, aceapex_archive **out) {
+  if (!h_archive || !out || nbytes == 0) return ACEAPEX_EINVAL;
+  *out = nullptr;
+  aceapex_archive *A = new (std::nothrow) aceapex_archive();
+  if (!A) return ACEAPEX_ENOMEM;
+  const uint8_t *a = static_cast<const uint8_t *>(h_archive);
+  int rc = validate(a, nbytes, A);
+  if (rc) {
+    delete A;
+    return rc;
+  }
+  A->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete A;
+    return ACEAPEX_ECUDA;
+  }
+  std::vector<uint32_t> lut;
+  build_lut(a, lut);
+  std::vector<WorkItem> order;
+  level_order(A->dir, nullptr, A->h.n_seg, 0, order);
+  const Header &h = A->h;
+  bool okm = A->d_payload.alloc(std::max<uint64_t>(h.payload_bytes, 16)) == cudaSuccess &&
+             A->d_dir.alloc(std::max<uint64_t>(h.n_seg, 1)) == cudaSuccess &&
+             A->d_lut.alloc(4 * kScale) == cudaSuccess && A->d_flags.alloc(std::max<uint64_t>(h.n_seg, 1)) == cudaSuccess &&
+             A->d_order.alloc(std::max<uint64_t>(h.n_seg, 1)) == cudaSuccess && A->d_words.alloc(4) == cudaSuccess &&
+             A->d_blocked.alloc(std::max<uint64_t>(h.n_seg, 1)) == cudaSuccess;
+  if (!okm || !global_epoch(device)) {
+    A->release();
+    delete A;
+    return ACEAPEX_ENOMEM;
+  }
+  cudaError_t e = cudaSuccess;
+  if (h.payload_bytes) e = cudaMemcpy(A->d_payload.p, a + h.off_payload, h.payload_bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && h.n_seg) e = cudaMemcpy(A->d_dir.p, A->dir.data(), 24 * h.n_seg, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(A->d_lut.p, lut.data(), 4 * lut.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && h.n_seg)
+    e = cudaMemcpy(A->d_order.p, order.data(), sizeof(WorkItem) * h.n_seg, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(A->d_flags.p, 0, 4 * std::max<uint64_t>(h.n_seg, 1));
+  if (e == cudaSuccess) e = cudaMemset(A->d_words.p, 0, 16);
+  if (e == cudaSuccess) e = cudaMemset(A->d_blocked.p, 0, std::max<uint64_t>(h.n_seg, 1));
+  if (e != cudaSuccess) {
+    A->release();
+    delete A;
+    return ACEAPEX_ECUDA;
+  }
+  *out = A;
+  return ACEAPEX_OK;
+}
+
+void aceapex_close(aceapex_archive *a) {
+  if (!a) return;
+  cudaSetDevice(a->device);
+  cudaDeviceSynchronize();
+  a->release();
+  delete a;
+}
+
+uint64_t aceapex_decoded_size(const aceapex_archive *a) { return a ? a->h.n : 0; }
+
+int aceapex_get_stats(const aceapex_archive *a, aceapex_stats *st) {
+  if (!a || !st) return ACEAPEX_EINVAL;
+  *st = a->stats;
+  return ACEAPEX_OK;
+}
+
+int aceapex_decode_all(aceapex_archive *a, void *d_out, uint64_t out_cap, void *stream, aceapex_stats *opt_stats) {
+  if (!a || (!d_out && a->h.n)) return ACEAPEX_EINVAL;
+  if (out_cap < a->h.n) return ACEAPEX_ERANGE;
+  if (opt_stats) *opt_stats = a->stats;
+  if (a->h.n == 0) return ACEAPEX_OK;
+  if (cudaSetDevice(a->device) != cudaSuccess) return ACEAPEX_ECUDA;
+  int rc = ensure_scratch(a);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t *ge = global_epoch(a->device);
+  if (!ge) return ACEAPEX_ECUDA;
+  cudaError_t e = launch_begin(ge, a->epoch(), a->counter(), st);
+  if (e != cudaSuccess) return ACEAPEX_ECUDA;
+  DecodeLaunch L = base_launch(a);
+  L.view0 = linear_view(static_cast<uint8_t *>(d_out), 0);
+  L.work = a->d_order.p;
+  L.n_work = (uint32_t)a->h.n_seg;
+  return cuda_status(launch_decode(L, a->grid, kBlock, st));
+}
+
+int aceapex_decode_range(aceapex_archive *a, uint64_t lo, uint64_t hi, void *d_out, uint64_t out_cap, void *stream) {
+  if (!a || (!d_out && hi > lo)) return ACEAPEX_EINVAL;
+  if (lo > hi || hi > a->h.n || out_cap < hi - lo) return ACEAPEX_ERANGE;
+  if (hi == lo) return ACEAPEX_OK;
+  if (cudaSetDevice(a->device) != cudaSuccess) return ACEAPEX_ECUDA;
+  int rc = ensure_scratch(a);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  OutView v;
+  uint32_t n = 0;
+  rc = decode_closure(a, lo >> a->h.log2_S, (hi - 1) >> a->h.log2_S, st, &v, &n, true);
+  if (rc) return rc;
+  cudaError_t e = launch_gather(v, a->h.log2_S, lo, hi, static_cast<uint8_t *>(d_out) - 0, st);
+  if (e == cudaSuccess) e = launch_clear_pages(a->d_page.p, a->d_work.p, n, st);
+  return cuda_status(e);
+}
+
+int aceapex_read_lookup(const aceapex_archive *a, uint64_t read_id, uint64_t *byte_lo, uint64_t *byte_hi) {
+  if (!a || !byte_lo || !byte_hi || a->h.n_reads == 0) return ACEAPEX_EINVAL;
+  if (read_id >= a->h.n_reads) return ACEAPEX_ERANGE;
+  *byte_lo = a->reads[read_id];
+  *byte_hi = read_id + 1 < a->h.n_reads ? a->reads[read_id + 1] : a->h.n;
+  return ACEAPEX_OK;
+}
+
+int aceapex_last_error(aceapex_archive *a, int sync, void *stream) {
+  if (!a) return ACEAPEX_EINVAL;
+  if (cudaSetDevice(a->device) != cudaSuccess) return ACEAPEX_ECUDA;
+  cudaError_t e = sync ? (stream ? cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) : cudaDeviceSynchronize())
+                       : cudaSuccess;
+  if (e != cudaSuccess) return ACEAPEX_ECUDA;
+  uint32_t v = 0;
+  if (cudaMemcpy(&v, a->err(), 4, cudaMemcpyDeviceToHost) != cudaSuccess) return ACEAPEX_ECUDA;
+  if (v && cudaMemset(a->err(), 0, 4) != cudaSuccess) return ACEAPEX_ECUDA;
+  return v == 0 ? ACEAPEX_OK : (int)v;
+}
+
+int aceapex_set_wait_limit(aceapex_archive *a, uint64_t ns) {
+  if (!a) return ACEAPEX_EINVAL;
+  a->wait_ns = ns ? ns : kDefaultWaitNs;
+  return ACEAPEX_OK;
+}
+
+int aceapex_debug_block_segments(aceapex_archive *a, const uint32_t *segs, uint32_t n) {
+  if (!a || (n && !segs)) return ACEAPEX_EINVAL;
+  for (uint32_t i = 0; i < n; ++i)
+    if (segs[i] >= a->h.n_seg) return ACEAPEX_ERANGE;
+  if (cudaSetDevice(a->device) != cudaSuccess) return ACEAPEX_ECUDA;
+  std::vector<uint8_t> b(std::max<uint64_t>(a->h.n_seg, 1), 0);
+  for (uint32_t i = 0; i < n; ++i) b[segs[i]] = 1;
+  if (cudaMemcpy(a->d_blocked.p, b.data(), b.size(), cudaMemcpyHostToDevice) != cudaSuccess) return ACEAPEX_ECUDA;
+  a->any_blocked = n != 0;
+  return ACEAPEX_OK;
+}
+
+int aceapex_stream_range(aceapex_archive *a, uint64_t lo, uint64_t hi, uint64_t ring_bytes, uint64_t window,
+                         uint32_t *d_crc, void *stream) {
+  if (!a || !d_crc) return ACEAPEX_EINVAL;
+  const Header &h = a->h;
+  const uint64_t S = uint64_t(1) << h.log2_S;
+  if (h.D == 0 || window == 0 || window % S || lo % S) return ACEAPEX_EINVAL;
+  if (lo > hi || hi > h.n) return ACEAPEX_ERANGE;
+  if (hi == lo) return ACEAPEX_OK;
+  if (ring_bytes & (ring_bytes - 1)) return ACEAPEX_EINVAL;
+  if (ring_bytes < window + round16(h.D) + 2 * S) return ACEAPEX_EINVAL;
+  if (cudaSetDevice(a->device) != cudaSuccess) return ACEAPEX_ECUDA;
+  int rc = ensure_scratch(a);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (a->d_ring.n != ring_bytes) {
+    cudaStreamSynchronize(st);
+    if (a->d_ring.alloc(ring_bytes) != cudaSuccess) return ACEAPEX_ENOMEM;
+  }
+  const uint64_t seg_per_win = window / S + 1;
+  if (a->d_seg_crc.n < seg_per_win) {
+    cudaStreamSynchronize(st);
+    if (a->d_seg_crc.alloc(seg_per_win) != cudaSuccess) return ACEAPEX_ENOMEM;
+  }
+  OutView ring{};
+  ring.base = a->d_ring.p;
+  ring.origin = 0;
+  ring.mask = ring_bytes - 1;
+  uint32_t *ge = global_epoch(a->device);
+  if (!ge) return ACEAPEX_ECUDA;
+  cudaError_t e = cudaSuccess;
+  bool begun = false;
+  // prime: bytes [lo - D, lo) must be in the ring with this call's epoch
+  if (lo > 0) {
+    uint64_t p0 = lo > h.D ? ((lo - h.D) & ~(S - 1)) : 0;
+    OutView v;
+    uint32_t n = 0;
+    rc = decode_closure(a, p0 >> h.log2_S, (lo - 1) >> h.log2_S, st, &v, &n, true);
+    if (rc) return rc;
+    begun = true;
+    if ((e = launch_copy_view(v, ring, h.log2_S, p0, lo, st)) != cudaSuccess) return ACEAPEX_ECUDA;
+    if ((e = launch_clear_pages(a->d_page.p, a->d_work.p, n, st)) != cudaSuccess) return ACEAPEX_ECUDA;
+  }
+  // all windows' work lists, uploaded once
+  const uint64_t s_lo = lo >> h.log2_S, s_hi = (hi - 1) >> h.log2_S, ns = s_hi - s_lo + 1;
+  std::vector<WorkItem> work;
+  work.reserve(ns);
+  std::vector<uint64_t> wstart;
+  std::vector<uint32_t> segs;
+  for (uint64_t wa = lo; wa < hi; wa += window) {
+    uint64_t wb = std::min(hi, wa + window);
+    segs.clear();
+    for (uint64_t s = wa >> h.log2_S; s <= (wb - 1) >> h.log2_S; ++s) segs.push_back((uint32_t)s);
+    wstart.push_back(work.size());
+    level_order(a->dir, segs.data(), segs.size(), 0, work);
+  }
+  wstart.push_back(work.size());
+  if (a->d_work.n < work.size()) {
+    cudaStreamSynchronize(st);
+    if (a->d_work.alloc(work.size()) != cudaSuccess) return ACEAPEX_ENOMEM;
+  }
+  if (a->stage_work.reserve(work.size() * sizeof(WorkItem)) != cudaSuccess) return ACEAPEX_ENOMEM;
+  std::memcpy(a->stage_work.p, work.data(), work.size() * sizeof(WorkItem));
+  e = cudaMemcpyAsync(a->d_work.p, a->stage_work.p, work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st);
+  a->stage_work.mark(st);
+  if (e != cudaSuccess) return ACEAPEX_ECUDA;
+  DecodeLaunch L = base_launch(a);
+  L.view0 = ring;
+  for (size_t k = 0; k + 1 < wstart.size(); ++k) {
+    uint64_t wa = lo + k * window, wb = std::min(hi, wa + window);
+    if (!begun) {
+      e = launch_begin(ge, a->epoch(), a->counter(), st);
+      begun = true;
+    } else {
+      e = cudaMemsetAsync(a->counter(), 0, 4, st);
+    }
+    if (e != cudaSuccess) return ACEAPEX_ECUDA;
+    L.work = a->d_work.p + wstart[k];
+    L.n_work = (uint32_t)(wstart[k + 1] - wstart[k]);
+    if ((e = launch_decode(L, a->grid, kBlock, st)) != cudaSuccess) return ACEAPEX_ECUDA;
+    if ((e = launch_window_crc(ring, wa, wb, window, d_crc + k, a->d_seg_crc.p, h.log2_S, st)) != cudaSuccess)
+      return ACEAPEX_ECUDA;
+  }
+  return ACEAPEX_OK;
+}
+
+int aceapex_decode_batch(aceapex_archive *const *as, int n, void *const *d_outs, void *stream) {
+  if (!as || !d_outs || n <= 0) return ACEAPEX_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!as[i] || as[i]->device != as[0]->device || (!d_outs[i] && as[i]->h.n)) return ACEAPEX_EINVAL;
+  aceapex_archive *A = as[0];
+  if (cudaSetDevice(A->device) != cudaSuccess) return ACEAPEX_ECUDA;
+  int rc = ensure_scratch(A);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // merge all segments by level: counting sort over (level, archive, segment)
+  std::vector<WorkItem> work;
+  uint64_t total = 0;
+  for (int i = 0; i < n; ++i) total += as[i]->h.n_seg;
+  uint32_t cnt[257] = {};
+  for (int i = 0; i < n; ++i)
+    for (const SegRec &r : as[i]->dir) cnt[r.level + 1]++;
+  for (int l = 0; l < 256; ++l) cnt[l + 1] += cnt[l];
+  work.resize(total);
+  for (int i = 0; i < n; ++i)
+    for (uint64_t s = 0; s < as[i]->h.n_seg; ++s) work[cnt[as[i]->dir[s].level]++] = WorkItem{(uint32_t)i, (uint32_t)s};
+  if (total == 0) return ACEAPEX_OK;
+  std::vector<DevArchive> arcs(n);
+  std::vector<OutView> views(n);
+  for (int i = 0; i < n; ++i) {
+    arcs[i] = as[i]->dev();
+    views[i] = linear_view(static_cast<uint8_t *>(d_outs[i]), 0);
+  }
+  const uint64_t bytes = sizeof(DevArchive) * n + sizeof(OutView) * n + sizeof(WorkItem) * total;
+  if (A->d_batch_work.n < total || A->d_batch_arcs.n < (uint64_t)n) {
+    cudaStreamSynchronize(st);
+    if (A->d_batch_work.alloc(total) != cudaSuccess || A->d_batch_arcs.alloc(n) != cudaSuccess ||
+        A->d_batch_views.alloc(n) != cudaSuccess)
+      return ACEAPEX_ENOMEM;
+  }
+  if (A->stage_batch.reserve(bytes) != cudaSuccess) return ACEAPEX_ENOMEM;
+  uint8_t *p = static_cast<uint8_t *>(A->stage_batch.p);
+  std::memcpy(p, arcs.data(), sizeof(DevArchive) * n);
+  std::memcpy(p + sizeof(DevArchive) * n, views.data(), sizeof(OutView) * n);
+  std::memcpy(p + (sizeof(DevArchive) + sizeof(OutView)) * n, work.data(), sizeof(WorkItem) * total);
+  cudaError_t e = cudaMemcpyAsync(A->d_batch_arcs.p, p, sizeof(DevArchive) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(A->d_batch_views.p, p + sizeof(DevArchive) * n, sizeof(OutView) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(A->d_batch_work.p, p + (sizeof(DevArchive) + sizeof(OutView)) * n, sizeof(WorkItem) * total,
+                        cudaMemcpyHostToDevice, st);
+  A->stage_batch.mark(st);
+  if (e != cudaSuccess) return ACEAPEX_ECUDA;
+  uint32_t *ge = global_epoch(A->device);
+  if (!ge || launch_begin(ge, A->epoch(), A->counter(), st) != cudaSuccess) return ACEAPEX_ECUDA;
+  DecodeLaunch L = base_launch(A);
+  L.arcs = A->d_batch_arcs.p;
+  L.views = A->d_batch_views.p;
+  L.work = A->d_batch_work.p;
+  L.n_work = (uint32_t)total;
+  return cuda_status(launch_decode(L, A->grid, kBlock, st));
+}
+
+int aceapex_encode(const void *h_in, uint64_t n, uint32_t log2_B, uint32_t min_match, uint32_t max_level,
+                   uint64_t dist_bound, const uint64_t *h_reads, uint64_t n_reads, int threads, void **h_out,
+                   uint64_t *out_len) {
+  if (!h_out || !out_len || (n && !h_in) || (n_reads && !h_reads)) return ACEAPEX_EINVAL;
+  uint8_t *o = nullptr;
+  int rc = encode_archive(static_cast<const uint8_t *>(h_in), n, log2_B, min_match, max_level, dist_bound, h_reads,
+                          n_reads, threads, &o, out_len);
+  *h_out = o;
+  return rc;
+}
+
+void aceapex_free(void *p) { std::free(p); }
+
+uint64_t aceapex_fastq_index(const void *h_in, uint64_t n, uint64_t *h_out, uint64_t cap) {
+  if (!h_in) return 0;
+  return fastq_index(static_cast<const uint8_t *>(h_in), n, h_out, cap);
+}
+
+}  // extern "C"

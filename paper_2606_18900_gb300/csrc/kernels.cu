@@ -1,0 +1,454 @@
+// GB300 (sm_103a) kernels of the device-resident decode path.
+//
+// decode_kernel — one persistent launch decodes a list of segments (paper
+// §3.3 full pipeline; §4 range decode; §5 chunked range decode). Each warp
+// repeatedly takes the next work item from a global counter; the list is in
+// level order, so every segment a warp waits for was taken earlier by a warp
+// that is running (no deadlock, FORMAT.md §2 levels). Per segment:
+//   1. entropy phase: the 32 lanes run the 32 interleaved rANS states of the
+//      segment (FORMAT.md §4); the step's renormalisation words are handed out
+//      in ascending lane order with a ballot + popc, from a 64-word register
+//      window that is refilled 32 words at a time; symbols go to the warp's
+//      staging buffer. No dependency is needed for this phase.
+//   2. command phase: 32 commands at a time (one per lane) are parsed from the
+//      staged streams, positions come from warp scans, every rule of FORMAT.md
+//      §2 is checked, and each match's source segments are checked (level
+//      below ours, present in the view) and waited for (bounded wait on their
+//      ready flags). Then the warp copies the literal run and the match of
+//      each command in order, so intra-segment chains see earlier output.
+//   3. publish: every lane fences, then lane 0 stores the epoch into the
+//      segment's flag with release semantics.
+// Errors latch the first code into a device word; waits give up at a time
+// limit (globaltimer) or as soon as another warp has latched an error.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace aceapex {
+
+namespace {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ void latch(uint32_t *err, uint32_t code) { atomicCAS(err, 0u, code); }
+
+// address of absolute position p in view v; nullptr when p's page is absent
+__device__ __forceinline__ uint8_t *at(const OutView &v, uint64_t p, uint32_t log2_S) {
+  if (v.page) {
+    uint32_t slot = v.page[p >> log2_S];
+    if (slot == 0xFFFFFFFFu) return nullptr;
+    return v.slot_base + ((uint64_t)slot << log2_S) + (p & ((uint64_t(1) << log2_S) - 1));
+  }
+  return v.base + ((p - v.origin) & v.mask);
+}
+
+// inclusive warp scan of a 32-bit value
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t t = __shfl_up_sync(kFull, v, d);
+    if (lane >= d) v += t;
+  }
+  return v;
+}
+
+// Wait until every lane with `need` sees *flag == epoch. False on timeout or
+// when another warp has latched an error.
+__device__ bool wait_flags(const uint32_t *flag, bool need, uint32_t epoch, uint64_t deadline, uint32_t *err,
+                           int lane) {
+  for (uint32_t spin = 0;; ++spin) {
+    bool ok = !need || ld_acquire(flag) == epoch;
+    if (__all_sync(kFull, ok)) return true;
+    if (ld_relaxed(err) != 0) return false;
+    if (now_ns() > deadline) {
+      if (lane == 0) latch(err, kErrTimeout);
+      return false;
+    }
+    __nanosleep(spin < 16 ? 32 : 256);
+  }
+}
+
+// Decode one segment into view V and publish its ready flag.
+__device__ void decode_segment(const DecodeLaunch &L, const DevArchive &A, const OutView &V, uint32_t seg,
+                               uint32_t epoch, uint8_t *stage, int lane) {
+  const uint32_t log2_S = A.log2_S;
+  const uint64_t seg_start = (uint64_t)seg << log2_S;
+  const uint64_t rem = A.n - seg_start;
+  const uint32_t out_size = rem < (uint64_t(1) << log2_S) ? (uint32_t)rem : (1u << log2_S);
+  const SegRec d = A.dir[seg];
+  const uint32_t nc = d.n_cmd, nl = d.n_lit, nw = d.n_words, W = A.W;
+  const uint32_t b1 = 2 * nc, b2 = 4 * nc, b3 = (4 + W) * nc, n_sym = b3 + nl;
+  bool ok = true;
+
+  // ---------------------------------------------------------------- rANS
+  const uint8_t *pl = A.payload + d.payload_off;
+  uint32_t x = __ldg(reinterpret_cast<const uint32_t *>(pl) + lane);
+  if (!__all_sync(kFull, x >= kRansL)) ok = false;
+  const uint16_t *words = reinterpret_cast<const uint16_t *>(pl + 128);
+  uint32_t w0 = lane < nw ? __ldg(words + lane) : 0u;
+  uint32_t w1 = lane + 32 < nw ? __ldg(words + lane + 32) : 0u;
+  uint32_t base = 0, wp = 0;
+  const uint32_t lt = lanemask_lt();
+  for (uint32_t t0 = 0; ok && t0 < n_sym; t0 += 32) {
+    const uint32_t q = t0 + lane;
+    const bool active = q < n_sym;
+    const uint32_t cls = q < b1 ? 0u : (q < b2 ? 1u : (q < b3 ? 2u : 3u));
+    uint32_t sym = 0;
+    if (active) {
+      const uint32_t e = __ldg(A.lut + (cls << kScaleBits) + (x & (kScale - 1)));
+      sym = e & 0xFFu;
+      x = ((e >> 20) + 1u) * (x >> kScaleBits) + ((e >> 8) & 0xFFFu);
+    }
+    const bool need = active && x < kRansL;
+    const uint32_t m = __ballot_sync(kFull, need);
+    const uint32_t k = (wp - base) + __popc(m & lt);  // < 64
+    const uint32_t lo = __shfl_sync(kFull, w0, k & 31);
+    const uint32_t hi = __shfl_sync(kFull, w1, k & 31);
+    if (need) x = (x << 16) | (k < 32 ? lo : hi);
+    wp += __popc(m);
+    if (wp - base >= 32) {
+      base += 32;
+      w0 = w1;
+      w1 = base + 32 + lane < nw ? __ldg(words + base + 32 + lane) : 0u;
+    }
+    if (active) stage[q] = (uint8_t)sym;
+  }
+  if (!__all_sync(kFull, x == kRansL) || wp != nw) ok = false;
+  __syncwarp();
+
+  // ------------------------------------------------------------ commands
+  const uint64_t deadline = now_ns() + L.wait_ns;
+  const uint32_t my_level = d.level;
+  uint32_t pos = 0, litc = 0;
+  for (uint32_t c0 = 0; ok && c0 < nc; c0 += 32) {
+    const uint32_t c = c0 + lane;
+    const bool valid = c < nc;
+    uint32_t ll = 0, ml = 0;
+    uint64_t src = 0;
+    if (valid) {
+      ll = (uint32_t)stage[2 * c] | ((uint32_t)stage[2 * c + 1] << 8);
+      ml = ((uint32_t)stage[b1 + 2 * c] | ((uint32_t)stage[b1 + 2 * c + 1] << 8)) + A.min_match;
+      for (uint32_t b = 0; b < W; ++b) src |= (uint64_t)stage[b2 + W * c + b] << (8 * b);
+    }
+    const uint32_t tot = ll + ml;
+    const uint32_t inc_t = warp_incl_scan(tot, lane), inc_l = warp_incl_scan(ll, lane);
+    const uint32_t sum_t = __shfl_sync(kFull, inc_t, 31), sum_l = __shfl_sync(kFull, inc_l, 31);
+    const uint32_t cpos = pos + inc_t - tot, clit = litc + inc_l - ll;
+    const uint64_t dst = seg_start + cpos + ll;
+    bool bad = valid && ((uint64_t)cpos + tot > out_size || (uint64_t)clit + ll > nl || src + ml > dst ||
+                         src + ml < src || (A.D && dst - src > A.D));
+    // source segments: ours, or of a lower level and present in the view
+    uint64_t q0 = 0, q1 = 0;
+    if (valid && !bad) {
+      q0 = src >> log2_S;
+      q1 = (src + ml - 1) >> log2_S;
+      for (uint64_t qq = q0; qq <= q1; ++qq) {
+        if (qq == seg) continue;
+        if (A.dir[qq].level >= my_level) bad = true;
+        if (V.page && V.page[qq] == 0xFFFFFFFFu) bad = true;
+      }
+    }
+    if (__any_sync(kFull, bad)) {
+      ok = false;
+      if (lane == 0) latch(L.err, kErrCorrupt);
+      break;
+    }
+    // bounded waits on the (at most two) source segments of each match
+    const bool need0 = valid && q0 != seg;
+    const bool need1 = valid && q1 != q0 && q1 != seg;
+    if (!wait_flags(A.flags + (need0 ? q0 : 0), need0, epoch, deadline, L.err, lane) ||
+        !wait_flags(A.flags + (need1 ? q1 : 0), need1, epoch, deadline, L.err, lane)) {
+      ok = false;
+      break;
+    }
+    __syncwarp();
+    const uint32_t n_here = nc - c0 < 32 ? nc - c0 : 32;
+    for (uint32_t j = 0; j < n_here; ++j) {
+      const uint32_t jll = __shfl_sync(kFull, ll, j), jml = __shfl_sync(kFull, ml, j);
+      const uint32_t jpos = __shfl_sync(kFull, cpos, j), jlit = __shfl_sync(kFull, clit, j);
+      const uint64_t jsrc = __shfl_sync(kFull, src, j);
+      for (uint32_t k = lane; k < jll; k += 32) *at(V, seg_start + jpos + k, log2_S) = stage[b3 + jlit + k];
+      const uint64_t d0 = seg_start + jpos + jll;
+      for (uint32_t k = lane; k < jml; k += 32) *at(V, d0 + k, log2_S) = __ldcg(at(V, jsrc + k, log2_S));
+      __syncwarp();
+    }
+    pos += sum_t;
+    litc += sum_l;
+  }
+  if (ok) {
+    const uint32_t trail = out_size - pos;
+    if (pos > out_size || litc + trail != nl) {
+      ok = false;
+      if (lane == 0) latch(L.err, kErrCorrupt);
+    } else {
+      for (uint32_t k = lane; k < trail; k += 32) *at(V, seg_start + pos + k, log2_S) = stage[b3 + litc + k];
+    }
+  } else if (lane == 0 && ld_relaxed(L.err) == 0) {
+    latch(L.err, kErrCorrupt);
+  }
+
+  // ------------------------------------------------------------- publish
+  __threadfence();
+  __syncwarp();
+  if (lane == 0 && ok && !(A.blocked && A.blocked[seg])) st_release(A.flags + seg, epoch);
+}
+
+__global__ void __launch_bounds__(256) decode_kernel(DecodeLaunch L) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t gwarp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (gwarp >= L.scratch_warps) return;
+  uint8_t *stage = L.scratch + (size_t)gwarp * kStageBytes;
+  const uint32_t epoch = ld_relaxed(L.epoch);
+  for (;;) {
+    uint32_t idx = 0;
+    if (lane == 0) idx = atomicAdd(L.counter, 1u);
+    idx = __shfl_sync(kFull, idx, 0);
+    if (idx >= L.n_work) break;
+    if (ld_relaxed(L.err) != 0) continue;  // drain the list quickly after an error
+    const WorkItem w = L.work[idx];
+    if (L.arcs) decode_segment(L, L.arcs[w.arc], L.views[w.arc], w.seg, epoch, stage, lane);
+    else decode_segment(L, L.arc0, L.view0, w.seg, epoch, stage, lane);
+  }
+}
+
+__global__ void begin_kernel(uint32_t *global_epoch, uint32_t *epoch, uint32_t *counter) {
+  *epoch = atomicAdd(global_epoch, 1u) + 1u;
+  *counter = 0;
+}
+
+__global__ void clear_pages_kernel(uint32_t *page, const WorkItem *work, uint32_t n) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) page[work[i].seg] = 0xFFFFFFFFu;
+}
+
+__global__ void copy_view_kernel(OutView src, OutView dst, uint32_t log2_S, uint64_t lo, uint64_t n) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint8_t *p = at(src, lo + i, log2_S);
+    uint8_t *q = at(dst, lo + i, log2_S);
+    if (p && q) *q = *p;
+  }
+}
+
+__global__ void gather_kernel(OutView v, uint32_t log2_S, uint64_t lo, uint64_t n, uint8_t *dst) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint8_t *p = at(v, lo + i, log2_S);
+    dst[i] = p ? *p : 0;
+  }
+}
+
+__global__ void set_pages_kernel(uint32_t *page, const WorkItem *work, uint32_t n) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) page[work[i].seg] = i;
+}
+
+// ------------------------------------------------------------------- CRC-32
+// Standard CRC-32 (reflected polynomial 0xEDB88320, init and xorout ~0).
+// A register r advanced over a message M from r0 is shift(r0, |M|) ^ raw(M),
+// where raw is the register from r0 = 0 and shift(r, L) multiplies by x^(8L)
+// mod P. So crc(A||B) = shift(crc(A), |B|) ^ crc(B), and crc(M) =
+// raw(M) ^ shift(~0, |M|) ^ ~0. shift() applies 32x32 GF(2) matrices for
+// L = 2^k bytes, built on the host by repeated squaring.
+__constant__ uint32_t c_crc_table[256];
+__constant__ uint32_t c_shift_op[48][32];  // op[k]: multiply by x^(8 * 2^k)
+
+__device__ __forceinline__ uint32_t gf2_apply(const uint32_t *op, uint32_t v) {
+  uint32_t r = 0;
+#pragma unroll 8
+  for (int i = 0; i < 32; ++i)
+    if (v >> i & 1u) r ^= op[i];
+  return r;
+}
+
+__device__ uint32_t crc_shift(uint32_t r, uint64_t len) {
+  for (int k = 0; len; ++k, len >>= 1)
+    if (len & 1) r = gf2_apply(c_shift_op[k], r);
+  return r;
+}
+
+// standard CRC of each segment piece [max(lo, seg), min(hi, seg_end)) of the view
+__global__ void seg_crc_kernel(OutView v, uint32_t log2_S, uint64_t lo, uint64_t hi, uint32_t *seg_crc) {
+  __shared__ uint32_t tab[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) tab[i] = c_crc_table[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint64_t S = uint64_t(1) << log2_S;
+  const uint64_t first = lo >> log2_S, last = (hi - 1) >> log2_S;
+  const uint64_t nseg = last - first + 1;
+  for (uint64_t i = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < nseg;
+       i += (uint64_t)gridDim.x * (blockDim.x >> 5)) {
+    const uint64_t s = first + i;
+    const uint64_t a = (s << log2_S) > lo ? (s << log2_S) : lo;
+    const uint64_t b = ((s << log2_S) + S) < hi ? ((s << log2_S) + S) : hi;
+    const uint64_t len = b - a, chunk = (len + 31) / 32;
+    const uint64_t ca = a + lane * chunk, cb = ca + chunk < b ? ca + chunk : b;
+    uint32_t r = 0;
+    const uint8_t *p = ca < b ? at(v, ca, log2_S) : nullptr;
+    for (uint64_t k = 0; ca + k < cb; ++k) r = (r >> 8) ^ tab[(r ^ __ldcg(p + k)) & 0xFFu];
+    // fold lanes: raw(A||B) = shift(raw(A), |B|) ^ raw(B); shift each lane's
+    // register past the bytes that follow its chunk, then XOR all lanes
+    r = crc_shift(r, ca < b ? b - cb : 0);
+#pragma unroll
+    for (int d = 16; d; d >>= 1) r ^= __shfl_xor_sync(kFull, r, d);
+    if (lane == 0) seg_crc[i] = r ^ crc_shift(0xFFFFFFFFu, len) ^ 0xFFFFFFFFu;
+  }
+}
+
+// one block per window: crc(window) from its pieces' CRCs
+__global__ void window_crc_kernel(const uint32_t *seg_crc, uint64_t lo, uint64_t hi, uint64_t window,
+                                  uint32_t log2_S, uint32_t *out) {
+  __shared__ uint32_t part[1024];
+  __shared__ uint64_t plen[1024];
+  const uint64_t k = blockIdx.x;
+  const uint64_t wa = lo + k * window, wb = wa + window < hi ? wa + window : hi;
+  const uint64_t first = lo >> log2_S;
+  const uint64_t s0 = wa >> log2_S, s1 = (wb - 1) >> log2_S;  // pieces of this window
+  const uint64_t np = s1 - s0 + 1;
+  const uint64_t per = (np + blockDim.x - 1) / blockDim.x;
+  const uint64_t i0 = threadIdx.x * per, i1 = i0 + per < np ? i0 + per : np;
+  uint32_t acc = 0;
+  uint64_t alen = 0;
+  for (uint64_t i = i0; i < i1; ++i) {
+    const uint64_t s = s0 + i;
+    const uint64_t a = (s << log2_S) > wa ? (s << log2_S) : wa;
+    const uint64_t e = ((s + 1) << log2_S) < wb ? ((s + 1) << log2_S) : wb;
+    acc = crc_shift(acc, e - a) ^ seg_crc[s - first];
+    alen += e - a;
+  }
+  part[threadIdx.x] = acc;
+  plen[threadIdx.x] = alen;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t c = 0;
+    for (uint32_t t = 0; t < blockDim.x; ++t)
+      if (plen[t]) c = crc_shift(c, plen[t]) ^ part[t];
+    out[k] = c;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+
+int decode_grid(int device, int block) {
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_kernel, block, 0);
+  if (per_sm < 1) per_sm = 1;
+  return sms * per_sm;
+}
+
+cudaError_t launch_decode(const DecodeLaunch &L, int grid, int block, cudaStream_t st) {
+  if (L.n_work == 0) return cudaSuccess;
+  decode_kernel<<<grid, block, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_begin(uint32_t *global_epoch, uint32_t *epoch, uint32_t *counter, cudaStream_t st) {
+  begin_kernel<<<1, 1, 0, st>>>(global_epoch, epoch, counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_clear_pages(uint32_t *page, const WorkItem *work, uint32_t n, cudaStream_t st) {
+  if (!n) return cudaSuccess;
+  clear_pages_kernel<<<(n + 255) / 256, 256, 0, st>>>(page, work, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_view(OutView src, OutView dst, uint32_t log2_S, uint64_t lo, uint64_t hi, cudaStream_t st) {
+  if (hi <= lo) return cudaSuccess;
+  uint64_t n = hi - lo;
+  int grid = (int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
+  copy_view_kernel<<<grid, 256, 0, st>>>(src, dst, log2_S, lo, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(OutView v, uint32_t log2_S, uint64_t lo, uint64_t hi, uint8_t *dst, cudaStream_t st) {
+  if (hi <= lo) return cudaSuccess;
+  uint64_t n = hi - lo;
+  int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  gather_kernel<<<grid, 256, 0, st>>>(v, log2_S, lo, n, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_pages(uint32_t *page, const WorkItem *work, uint32_t n, cudaStream_t st) {
+  if (!n) return cudaSuccess;
+  set_pages_kernel<<<(n + 255) / 256, 256, 0, st>>>(page, work, n);
+  return cudaGetLastError();
+}
+
+static bool g_crc_ready[64] = {};
+
+static cudaError_t ensure_crc_constants() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && g_crc_ready[dev]) return cudaSuccess;
+  uint32_t tab[256];
+  for (uint32_t b = 0; b < 256; ++b) {
+    uint32_t c = b;
+    for (int k = 0; k < 8; ++k) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+    tab[b] = c;
+  }
+  // op[0]: one zero byte; column i = register 1<<i advanced by 8 zero bits
+  static uint32_t op[48][32];
+  for (int i = 0; i < 32; ++i) {
+    uint32_t c = 1u << i;
+    for (int k = 0; k < 8; ++k) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+    op[0][i] = c;
+  }
+  for (int k = 1; k < 48; ++k)
+    for (int i = 0; i < 32; ++i) {
+      uint32_t v = op[k - 1][i], r = 0;
+      for (int j = 0; j < 32; ++j)
+        if (v >> j & 1u) r ^= op[k - 1][j];
+      op[k][i] = r;
+    }
+  cudaError_t e = cudaMemcpyToSymbol(c_crc_table, tab, sizeof(tab));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_shift_op, op, sizeof(op));
+  if (e == cudaSuccess && dev >= 0 && dev < 64) g_crc_ready[dev] = true;
+  return e;
+}
+
+cudaError_t launch_window_crc(OutView v, uint64_t lo, uint64_t hi, uint64_t window, uint32_t *crc, uint32_t *seg_crc,
+                              uint32_t log2_S, cudaStream_t st) {
+  if (hi <= lo) return cudaSuccess;
+  cudaError_t e = ensure_crc_constants();
+  if (e != cudaSuccess) return e;
+  const uint64_t nseg = ((hi - 1) >> log2_S) - (lo >> log2_S) + 1;
+  int grid = (int)((nseg + 7) / 8 < 65535 ? (nseg + 7) / 8 : 65535);
+  seg_crc_kernel<<<grid, 256, 0, st>>>(v, log2_S, lo, hi, seg_crc);
+  const uint64_t nwin = (hi - lo + window - 1) / window;
+  window_crc_kernel<<<(unsigned)nwin, 256, 0, st>>>(seg_crc, lo, hi, window, log2_S, crc);
+  return cudaGetLastError();
+}
+
+}  // namespace aceapex

@@ -1,0 +1,95 @@
+// Device-side data structures and the launchers that host.cpp calls.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "format.h"
+
+namespace aceapex {
+
+// Device error word values (match aceapex_status).
+constexpr uint32_t kErrCorrupt = 2;
+constexpr uint32_t kErrTimeout = 5;
+
+// One archive as the kernels see it (all pointers are device pointers).
+struct DevArchive {
+  const uint8_t *payload;   // payload section (segment payloads, 16-byte aligned)
+  const SegRec *dir;        // segment directory
+  const uint64_t *dep_ptr;  // n_seg + 1
+  const uint32_t *deps;     // dependency lists
+  const uint32_t *lut;      // 4 classes x 4096 slots: sym | bias << 8 | (freq - 1) << 20
+  uint32_t *flags;          // per-segment ready flag (= epoch when complete)
+  const uint8_t *blocked;   // test hook: per-segment "never publish" bytes, or nullptr
+  uint64_t n;               // decompressed size
+  uint64_t D;               // distance bound (0 = none)
+  uint32_t log2_S, W, min_match, n_seg;
+};
+
+// Where absolute output position p lives.
+//  linear / ring: base + ((p - origin) & mask)   (mask = ~0 for linear)
+//  paged:         slot_base + page[p >> log2_S] * S + (p & (S - 1))
+struct OutView {
+  uint8_t *base;
+  uint64_t origin;
+  uint64_t mask;
+  const uint32_t *page;  // non-null selects paged addressing
+  uint8_t *slot_base;
+};
+
+// A unit of work: archive index (batch) and segment.
+struct WorkItem {
+  uint32_t arc;
+  uint32_t seg;
+};
+
+struct DecodeLaunch {
+  DevArchive arc0;          // single-archive launches
+  OutView view0;
+  const DevArchive *arcs;   // batch launches: device arrays indexed by WorkItem::arc (else nullptr)
+  const OutView *views;
+  const WorkItem *work;     // device array in dependency-respecting order
+  uint32_t n_work;
+  const uint32_t *epoch;    // device word written by the begin kernel of this call
+  uint32_t *counter;        // work counter, zeroed by the begin kernel
+  uint32_t *err;            // device error word
+  uint8_t *scratch;         // per-warp staging, kStageBytes each
+  uint64_t wait_ns;         // dependency wait limit
+  uint32_t scratch_warps;   // number of per-warp staging slots
+};
+
+constexpr uint32_t kStageBytes = kMaxSym;  // decoded symbols of one segment
+
+struct LaunchShape {
+  int grid;
+  int block;
+};
+
+// Start of a decode call: *epoch = ++*global_epoch, *counter = 0 (one thread).
+// Keeping the epoch in device memory makes replays of a captured graph use
+// fresh epochs.
+cudaError_t launch_begin(uint32_t *global_epoch, uint32_t *epoch, uint32_t *counter, cudaStream_t st);
+
+// Persistent decode over L.work.
+cudaError_t launch_decode(const DecodeLaunch &L, int grid, int block, cudaStream_t st);
+
+// page[work[i].seg] = 0xFFFFFFFF for i < n (undo launch_set_pages)
+cudaError_t launch_clear_pages(uint32_t *page, const WorkItem *work, uint32_t n, cudaStream_t st);
+
+// copy [lo, hi) from view src to view dst (both addressed by absolute position)
+cudaError_t launch_copy_view(OutView src, OutView dst, uint32_t log2_S, uint64_t lo, uint64_t hi, cudaStream_t st);
+
+// Occupancy-derived grid for the decode kernel.
+int decode_grid(int device, int block);
+
+// Gather [lo, hi) through a view into a flat buffer.
+cudaError_t launch_gather(OutView v, uint32_t log2_S, uint64_t lo, uint64_t hi, uint8_t *dst, cudaStream_t st);
+
+// page[work[i].seg] = i for i < n (paged views)
+cudaError_t launch_set_pages(uint32_t *page, const WorkItem *work, uint32_t n, cudaStream_t st);
+
+// CRC-32 of each window [lo + k*window, ...) of the ring view, written to crc[k].
+cudaError_t launch_window_crc(OutView v, uint64_t lo, uint64_t hi, uint64_t window, uint32_t *crc, uint32_t *seg_crc,
+                              uint32_t log2_S, cudaStream_t st);
+
+}  // namespace aceapex

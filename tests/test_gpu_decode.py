@@ -1,0 +1,268 @@
+"""GPU parity: every decode path of libaceapex.so (called through its C ABI)
+must reproduce the oracle's decoded bytes exactly (integer work: bit-exact).
+Archives come from the oracle encoder and from the library encoder; expected
+bytes come from the oracle decoder and from the generator's original input."""
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2606_18900_gb300 as ace
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+def gpu_decode_all(arc_bytes, stream=None):
+    with ace.Archive(arc_bytes) as a:
+        n = a.size
+        out = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
+        a.decode_all(out, stream)
+        a.check(stream)
+        return out[:n].cpu().numpy()
+
+
+def assert_same(got, want):
+    assert got.size == want.size
+    if not np.array_equal(got, want):
+        bad = np.nonzero(got != want)[0]
+        raise AssertionError(f"{bad.size} bytes differ, first at {bad[0]} (of {want.size})")
+
+
+# ------------------------------------------------------------------ whole file
+
+def test_tiny_fastq_oracle_archive():
+    d = synth.tiny_fastq()
+    a = oracle.encode(d, reads=oracle.fastq_record_starts(d))
+    want = oracle.decode(a)
+    assert_same(want, d)
+    assert_same(gpu_decode_all(a), want)
+
+
+def test_tiny_fastq_library_archive():
+    d = synth.tiny_fastq()
+    a = ace.encode(d, min_match=16)
+    assert_same(gpu_decode_all(a), oracle.decode(a))
+
+
+def test_worked_example():
+    from conftest import load_hex_fixture
+    arc, meta = load_hex_fixture("abab_archive.txt")
+    assert gpu_decode_all(arc).tobytes() == bytes.fromhex(meta["output"][0])
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 255, 16383, 16384, 16385, 100_003])
+def test_sizes_and_ragged_tails(n):
+    d = synth.random_bytes(3, n, n, b"ACGT")
+    if n > 200:
+        d[n // 2: n // 2 + 100] = d[10:110]
+    for enc in (oracle.encode, ace.encode):
+        a = enc(d, min_match=4)
+        assert_same(gpu_decode_all(a), oracle.decode(a))
+
+
+@pytest.mark.parametrize("log2_B", [2, 3, 4, 6, 9, 12])
+def test_small_blocks_many_segments(log2_B):
+    """Tiny segments: many levels, intra-segment chains and sources that span
+    two segments."""
+    d = synth.random_bytes(4, log2_B, 20_000, b"ab")
+    for enc, kw in ((oracle.encode, dict(chain=64)), (ace.encode, {})):
+        a = enc(d, log2_B=log2_B, min_match=2, max_level=8, **kw)
+        assert_same(gpu_decode_all(a), oracle.decode(a))
+
+
+@pytest.mark.parametrize("alpha", [b"a", b"ab", b"ACGT", bytes(range(256))])
+def test_alphabets(alpha):
+    d = synth.random_bytes(5, len(alpha), 70_000, alpha)
+    a = oracle.encode(d, min_match=4)
+    assert_same(gpu_decode_all(a), d)
+
+
+def test_runs_and_periodic():
+    d = np.concatenate([np.full(50_000, 78, np.uint8), np.frombuffer(b"ACGTTGCA" * 9000, np.uint8),
+                        np.full(3, 65, np.uint8)])
+    for enc in (oracle.encode, ace.encode):
+        a = enc(d, min_match=8)
+        assert_same(gpu_decode_all(a), d)
+
+
+@pytest.mark.parametrize("cap", [0, 1, 2, 8, 30])
+def test_level_caps(cap):
+    d = synth.pe_fastq(3 << 20, ref_len=1_000_000)
+    a = ace.encode(d, max_level=cap, min_match=12)
+    assert_same(gpu_decode_all(a), d)
+
+
+@pytest.mark.parametrize("log2_B", [14, 20])
+def test_medium_fastq_block_sizes(log2_B):
+    d = synth.pe_fastq(24 << 20, ref_len=5_000_000)
+    a = ace.encode(d, log2_B=log2_B, min_match=16)
+    assert_same(gpu_decode_all(a), d)
+    b = oracle.encode(d[: 4 << 20], log2_B=log2_B)
+    assert_same(gpu_decode_all(b), oracle.decode(b))
+
+
+def test_fasta_with_distance_bound():
+    d = synth.fasta(6_000_000, seed=11, n_chrom=4)
+    a = ace.encode(d, dist_bound=1 << 20, min_match=12)
+    assert_same(gpu_decode_all(a), d)
+
+
+def test_repeat_decode_same_handle_and_streams():
+    d = synth.tiny_fastq()
+    a = ace.encode(d, min_match=16)
+    with ace.Archive(a) as arc:
+        s = torch.cuda.Stream()
+        for i in range(4):
+            out = torch.zeros(arc.size, dtype=torch.uint8, device="cuda")
+            arc.decode_all(out, s if i % 2 else None)
+            arc.check(s if i % 2 else None)
+            assert_same(out.cpu().numpy(), d)
+
+
+def test_cuda_graph_replay():
+    d = synth.tiny_fastq()
+    a = ace.encode(d, min_match=16)
+    with ace.Archive(a) as arc:
+        out = torch.zeros(arc.size, dtype=torch.uint8, device="cuda")
+        s = torch.cuda.Stream()
+        arc.decode_all(out, s)        # first call allocates scratch outside capture
+        arc.check(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            arc.decode_all(out, s)
+        for _ in range(3):
+            out.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            assert arc.last_error() == ace.OK
+            assert_same(out.cpu().numpy(), d)
+
+
+# ------------------------------------------------------------- range / lookup
+
+def test_decode_range_random_ranges():
+    d = synth.pe_fastq(8 << 20, ref_len=2_000_000)
+    a = ace.encode(d, min_match=16)
+    rng = np.random.default_rng(1)
+    with ace.Archive(a) as arc:
+        cases = [(0, 1), (0, d.size), (d.size - 1, d.size), (16383, 16385), (5, 5)]
+        for _ in range(20):
+            lo = int(rng.integers(0, d.size))
+            hi = int(min(d.size, lo + rng.integers(1, 300_000)))
+            cases.append((lo, hi))
+        for lo, hi in cases:
+            out = torch.zeros(max(hi - lo, 1), dtype=torch.uint8, device="cuda")
+            arc.decode_range(lo, hi, out)
+            arc.check()
+            assert_same(out[: hi - lo].cpu().numpy(), d[lo:hi])
+
+
+def test_read_lookup_then_decode():
+    d = synth.tiny_fastq()
+    reads = oracle.fastq_record_starts(d)
+    a = ace.encode(d, reads=ace.fastq_index(d), min_match=16)
+    text = d.tobytes()
+    with ace.Archive(a) as arc:
+        for r in [0, 1, 2, 777, 1998, 1999]:
+            lo, hi = arc.read_lookup(r)
+            assert lo == reads[r] and hi == (reads[r + 1] if r + 1 < len(reads) else d.size)
+            out = torch.zeros(hi - lo, dtype=torch.uint8, device="cuda")
+            arc.decode_range(lo, hi, out)
+            arc.check()
+            rec = out.cpu().numpy().tobytes()
+            assert rec == text[lo:hi] and rec.startswith(b"@SIM:") and rec.count(b"\n") == 4
+        with pytest.raises(ace.AceapexError):
+            arc.read_lookup(2000)
+
+
+# -------------------------------------------------------------- ring streaming
+
+@pytest.mark.parametrize("lo", [0, 3 << 14])
+def test_stream_range_crcs(lo):
+    d = synth.fasta(5_000_000, seed=12, n_chrom=3)
+    D = 1 << 18
+    a = ace.encode(d, dist_bound=D, min_match=12)
+    window = 1 << 19
+    ring = 1 << 21
+    hi = d.size
+    with ace.Archive(a) as arc:
+        nw = (hi - lo + window - 1) // window
+        crc = torch.zeros(nw, dtype=torch.int32, device="cuda")
+        arc.stream_range(lo, hi, ring, window, crc)
+        arc.check()
+        got = [int(c) & 0xFFFFFFFF for c in crc.cpu().tolist()]
+    want = [zlib.crc32(d[b:min(hi, b + window)].tobytes()) for b in range(lo, hi, window)]
+    assert got == want
+    assert list(oracle.decode_stream_crcs(a, lo, hi, window)) == want
+
+
+# ------------------------------------------------------------------- batching
+
+def test_decode_batch():
+    sizes = [16384, 1, 50_000, 16385, 300_000, 2_000_000]
+    datas = [synth.random_bytes(9, i, s, b"ACGT") for i, s in enumerate(sizes)]
+    datas.append(synth.tiny_fastq())
+    arcs = [ace.Archive(ace.encode(x, min_match=6)) for x in datas]
+    outs = [torch.zeros(max(x.size, 1), dtype=torch.uint8, device="cuda") for x in datas]
+    ace.decode_batch(arcs, outs)
+    arcs[0].check()
+    for x, o in zip(datas, outs):
+        assert_same(o[: x.size].cpu().numpy(), x)
+    for a in arcs:
+        a.close()
+
+
+# -------------------------------------------------------------- failure paths
+
+def test_timeout_is_reported_and_context_survives():
+    d = synth.pe_fastq(2 << 20, ref_len=500_000)
+    a = ace.encode(d, min_match=12)
+    s = oracle.sections(a)
+    dep_of = np.nonzero(np.diff(s["dep_ptr"]))[0]
+    assert dep_of.size
+    victim = int(s["deps"][s["dep_ptr"][dep_of[0]]])
+    with ace.Archive(a) as arc:
+        arc.set_wait_limit(20_000_000)  # 20 ms
+        arc.debug_block_segments([victim])
+        out = torch.zeros(arc.size, dtype=torch.uint8, device="cuda")
+        arc.decode_all(out)
+        assert arc.last_error() == ace.ETIMEOUT
+        arc.debug_block_segments([])
+        arc.set_wait_limit(0)
+        arc.decode_all(out)
+        arc.check()
+        assert_same(out.cpu().numpy(), d)
+
+
+def test_corrupt_payload_is_reported():
+    d = synth.tiny_fastq()
+    a = ace.encode(d, min_match=16)
+    s = oracle.sections(a)
+    b = a.copy()
+    b[s["off_payload"]: s["off_payload"] + 4] = 0      # state below 2^16
+    with ace.Archive(b) as arc:
+        out = torch.zeros(arc.size, dtype=torch.uint8, device="cuda")
+        arc.decode_all(out)
+        assert arc.last_error() == ace.ECORRUPT
+        arc.decode_all(out)  # still usable
+        assert arc.last_error() == ace.ECORRUPT
+    with ace.Archive(a) as arc:
+        out = torch.zeros(arc.size, dtype=torch.uint8, device="cuda")
+        arc.decode_all(out)
+        arc.check()
+        assert_same(out.cpu().numpy(), d)
+
+
+def test_out_cap_checked():
+    a = ace.encode(synth.tiny_fastq(), min_match=16)
+    with ace.Archive(a) as arc:
+        small = torch.zeros(100, dtype=torch.uint8, device="cuda")
+        with pytest.raises(ace.AceapexError) as e:
+            arc.decode_all(small)
+        assert e.value.code == ace.ERANGE

@@ -1,0 +1,115 @@
+"""Host-side checks of libaceapex.so that need no GPU: the library builds and
+exports every entry point declared in include/aceapex.h; its encoder's
+archives decode exactly under the oracle (an independent implementation of
+FORMAT.md); archive validation rejects damaged headers before any device
+work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2606_18900_gb300 as ace
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(aceapex_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ace.lib()
+    names = declared_symbols()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_no_cpu_fallback_in_binding():
+    """The binding forwards to the library only (no numpy/torch decode path)."""
+    src = open(os.path.join(ROOT, "paper_2606_18900_gb300", "__init__.py")).read()
+    assert "import oracle" not in src and "from oracle" not in src
+
+
+@pytest.mark.parametrize("make", ["tiny", "random", "runs", "fasta"])
+@pytest.mark.parametrize("log2_B", [3, 10, 14, 20])
+def test_library_encoder_roundtrip_under_oracle(make, log2_B):
+    if make == "tiny":
+        d = synth.tiny_fastq()[:300_000]
+    elif make == "random":
+        d = synth.random_bytes(1, log2_B, 50_001, b"ACGT")
+    elif make == "runs":
+        d = np.repeat(np.frombuffer(b"ACGTN", np.uint8), [10000, 1, 30000, 7, 20000])
+    else:
+        d = synth.fasta(200_000, seed=2, n_chrom=2)
+    mm = 2 if log2_B == 3 else 0
+    a = ace.encode(d, log2_B=log2_B, min_match=mm)
+    assert np.array_equal(oracle.decode(a), d)
+    s = oracle.sections(a)
+    assert s["dir"]["level"].max(initial=0) <= s["max_level"]
+
+
+def test_library_encoder_params():
+    d = synth.tiny_fastq()
+    reads = ace.fastq_index(d)
+    assert np.array_equal(reads, oracle.fastq_record_starts(d))
+    for cap in (0, 1, 3, 8):
+        a = ace.encode(d, max_level=cap, reads=reads, min_match=16)
+        s = oracle.sections(a)
+        assert s["dir"]["level"].max(initial=0) <= cap
+        assert np.array_equal(s["reads"], reads)
+        assert np.array_equal(oracle.decode(a), d)
+    f = synth.fasta(500_000, seed=5, n_chrom=3)
+    a = ace.encode(f, log2_B=12, dist_bound=40_000, min_match=12)
+    s = oracle.sections(a)
+    assert s["D"] == 40_000
+    assert np.array_equal(oracle.decode(a), f)
+
+
+def test_library_encoder_deterministic_across_threads():
+    d = synth.pe_fastq(4 << 20, ref_len=2_000_000)
+    a1 = ace.encode(d, threads=1, min_match=16)
+    a8 = ace.encode(d, threads=8, min_match=16)
+    assert np.array_equal(a1, a8)
+
+
+def test_empty_input():
+    a = ace.encode(np.zeros(0, np.uint8))
+    assert oracle.decode(a).size == 0
+
+
+def _open_status(buf):
+    lib = ace.lib()
+    h = ctypes.c_void_p()
+    b = np.ascontiguousarray(buf, dtype=np.uint8)
+    return lib.aceapex_open(b.ctypes.data, b.size, 0, ctypes.byref(h))
+
+
+def test_open_rejects_damaged_archives():
+    a = ace.encode(synth.tiny_fastq()[:200_000], min_match=16)
+    assert _open_status(a[:-16]) == ace.ECORRUPT
+    for off, val in [(0, 0), (8, 2), (26, 7), (28, 11), (29, 16), (40, 99)]:
+        b = a.copy()
+        b[off] = val
+        assert _open_status(b) == ace.ECORRUPT, off
+    b = a.copy()
+    b[128 + 1] ^= 4          # table sum
+    assert _open_status(b) == ace.ECORRUPT
+    s = oracle.sections(a)
+    if s["n_deps"]:
+        b = a.copy()         # level of a segment with dependencies
+        seg = int(np.nonzero(np.diff(s["dep_ptr"]))[0][0])
+        b[128 + 2048 + 24 * seg + 20] ^= 1
+        assert _open_status(b) == ace.ECORRUPT
+    lib = ace.lib()
+    assert lib.aceapex_open(None, 10, 0, ctypes.byref(ctypes.c_void_p())) == ace.EINVAL
