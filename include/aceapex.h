@@ -153,6 +153,36 @@ int aceapex_stream_range(aceapex_archive *a, uint64_t byte_lo, uint64_t byte_hi,
 int aceapex_decode_batch(aceapex_archive *const *as, int n, void *const *d_outs, void *stream);
 
 /*
+ * Allocation-free whole-file decode. The paper has no counterpart; this entry
+ * point exists for callers that cannot allocate device memory when they
+ * decode: for example a program that gives all device memory to its own pool
+ * at start-up and forbids libraries from calling cudaMalloc afterwards, or a
+ * real-time pipeline that only allows allocation during initialisation. It
+ * calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * d_archive: the complete archive (FORMAT.md v1) in device memory, 16-byte
+ * aligned, nbytes long (caller-owned, read only). d_out: out_cap bytes of
+ * device memory that receive the decoded output. d_status: one device word
+ * that receives 0 or the aceapex_status of a device-side error once the work
+ * queued on `stream` has run. The header (128 bytes) is read to the host
+ * first, so the call synchronises `stream` once before queuing the decode.
+ *
+ * Scratch: a fixed array of about 4.3 MiB in the library's device memory,
+ * which every GPU that loads the library holds until the process exits. The
+ * first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture. Archives
+ * of more than 65,536 segments (1 GiB at 16 KiB segments) are rejected with
+ * ERANGE. All calls share the array and it keeps the last call's contents;
+ * each call resets what must start at zero, but calls that overlap on the
+ * GPU race and must not be issued. The decode uses 256 warps, so it is
+ * slower than aceapex_decode_all. Errors: EINVAL (null, misaligned or short
+ * archive), ECORRUPT (bad header), ERANGE (too many segments, out_cap < N),
+ * ECUDA.
+ */
+int aceapex_decode_all_noalloc(const void *d_archive, uint64_t nbytes, void *d_out, uint64_t out_cap,
+                               uint32_t *d_status, void *stream);
+
+/*
  * Host encoder (paper §2: global match search, absolute offsets, fixed
  * blocks; the paper's encoder is CPU-only too). Produces a FORMAT.md v1
  * archive of h_in[0..n) in a malloc'd buffer *h_out (*out_len bytes; free

@@ -112,6 +112,8 @@ def lib():
             L.aceapex_stream_range.argtypes = [vp, u64, u64, u64, u64, vp, vp]
             L.aceapex_decode_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), vp]
             L.aceapex_encode.argtypes = [vp, u64, u32, u32, u32, u64, u64p, u64, i32, ctypes.POINTER(vp), u64p]
+            L.aceapex_decode_all_noalloc.argtypes = [vp, u64, vp, u64, vp, vp]
+            L.aceapex_decode_all_noalloc.restype = i32
             L.aceapex_free.argtypes = [vp]
             L.aceapex_free.restype = None
             L.aceapex_fastq_index.argtypes = [vp, u64, u64p, u64]
@@ -263,6 +265,14 @@ class Archive:
         _check(lib().aceapex_debug_block_segments(
             self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)) if a.size else None, a.size),
             "aceapex_debug_block_segments")
+
+
+def decode_all_noalloc(d_archive, nbytes: int, out, status, stream=None) -> int:
+    """aceapex_decode_all_noalloc: the archive is already in device memory
+    (d_archive), nothing is allocated; returns the call's status code."""
+    cap = out.numel() * out.element_size()
+    return int(lib().aceapex_decode_all_noalloc(_ptr(d_archive), nbytes, _ptr(out), cap, _ptr(status),
+                                                _stream(stream)))
 
 
 def decode_batch(archives, outs, stream=None):

@@ -23,6 +23,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
+#include <mutex>
 
 #include "kernels.h"
 
@@ -449,6 +451,194 @@ cudaError_t launch_window_crc(OutView v, uint64_t lo, uint64_t hi, uint64_t wind
   const uint64_t nwin = (hi - lo + window - 1) / window;
   window_crc_kernel<<<(unsigned)nwin, 256, 0, st>>>(seg_crc, lo, hi, window, log2_S, crc);
   return cudaGetLastError();
+}
+
+// ===================================================================
+// Allocation-free whole-file decode (aceapex_decode_all_noalloc).
+//
+// Some callers cannot allocate device memory at decode time: a host program
+// that hands the whole device to its own memory pool at start-up and forbids
+// libraries from calling cudaMalloc afterwards, or a real-time pipeline that
+// only permits allocation during initialisation. For them this entry point
+// decodes an archive that the caller already holds in device memory into the
+// caller's output buffer and allocates nothing: the scratch it needs (decode
+// tables, ready flags, control words and per-warp staging) lives in one
+// file-scope device array of fixed size, which every GPU that loads the
+// library holds until the process exits.
+//
+// Limits: at most kNoAllocMaxSegments segments (1 GiB of output at 16 KiB
+// segments); larger archives are rejected with ACEAPEX_ERANGE. The decode
+// runs on kNoAllocWarps warps only, so it is slower than
+// aceapex_decode_all. All calls share the array and it keeps the last
+// call's contents: each call clears the words that must start at zero and
+// takes a fresh epoch, but calls that overlap on the GPU (on different
+// streams, or from different threads) race and must not be issued.
+namespace {
+
+constexpr uint32_t kNoAllocMaxSegments = 65536;
+constexpr uint32_t kNoAllocWarps = 256;
+constexpr size_t kNoAllocCtlBytes = 256;                       // counter, epoch, err
+constexpr size_t kNoAllocLutBytes = 4 * kScale * sizeof(uint32_t);
+constexpr size_t kNoAllocFlagBytes = kNoAllocMaxSegments * sizeof(uint32_t);
+constexpr size_t kNoAllocStageBytes = (size_t)kNoAllocWarps * kStageBytes;
+constexpr size_t kNoAllocBytes = kNoAllocCtlBytes + kNoAllocLutBytes + kNoAllocFlagBytes + kNoAllocStageBytes;
+
+// about 4.3 MiB per device
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];
+
+// control words at the start of the array
+constexpr size_t kCtlCounter = 0, kCtlEpoch = 4, kCtlErr = 8, kCtlEmpty = 12;
+
+// builds the decode table from the archive's tables, checks their sums,
+// clears the counter and the error word, and takes the next epoch
+__global__ void noalloc_setup_kernel(const uint8_t *tables) {
+  uint8_t *base = g_noalloc_scratch;
+  uint32_t *ctl = reinterpret_cast<uint32_t *>(base);
+  uint32_t *lut = reinterpret_cast<uint32_t *>(base + kNoAllocCtlBytes);
+  __shared__ uint32_t cum[4][257];
+  __shared__ uint32_t bad;
+  __shared__ uint32_t empty;
+  if (threadIdx.x == 0) {
+    bad = 0;
+    empty = 0;
+    for (int c = 0; c < 4; ++c) {
+      uint32_t s = 0;
+      cum[c][0] = 0;
+      for (int x = 0; x < 256; ++x) {
+        s += (uint32_t)tables[512 * c + 2 * x] | ((uint32_t)tables[512 * c + 2 * x + 1] << 8);
+        cum[c][x + 1] = s;
+      }
+      if (s != 0 && s != kScale) bad = 1;
+      if (s == 0) empty |= 1u << c;
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
+    const uint32_t c = i >> 8, x = i & 255, f = cum[c][x + 1] - cum[c][x];
+    for (uint32_t k = 0; k < f && !bad; ++k) lut[c * kScale + cum[c][x] + k] = x | (k << 8) | ((f - 1) << 20);
+  }
+  if (threadIdx.x == 0) {
+    ctl[kCtlCounter / 4] = 0;
+    ctl[kCtlErr / 4] = bad ? kErrCorrupt : 0u;
+    ctl[kCtlEmpty / 4] = empty;
+    ctl[kCtlEpoch / 4] = ctl[kCtlEpoch / 4] + 1u;
+  }
+}
+
+// segments in index order (every source segment precedes its reader, so a
+// warp only waits for segments that running warps took earlier)
+__global__ void __launch_bounds__(256) noalloc_decode_kernel(DecodeLaunch L, uint64_t payload_bytes,
+                                                             uint32_t max_level) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t gwarp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (gwarp >= kNoAllocWarps) return;
+  uint8_t *stage = g_noalloc_scratch + kNoAllocCtlBytes + kNoAllocLutBytes + kNoAllocFlagBytes +
+                   (size_t)gwarp * kStageBytes;
+  const uint32_t epoch = ld_relaxed(L.epoch);
+  const uint32_t empty = reinterpret_cast<const uint32_t *>(g_noalloc_scratch)[kCtlEmpty / 4];
+  const DevArchive &A = L.arc0;
+  for (;;) {
+    uint32_t seg = 0;
+    if (lane == 0) seg = atomicAdd(L.counter, 1u);
+    seg = __shfl_sync(kFull, seg, 0);
+    if (seg >= A.n_seg) break;
+    if (ld_relaxed(L.err) != 0) continue;
+    // the directory was not validated on the host: check what the shared
+    // segment decoder relies on before calling it
+    const SegRec d = A.dir[seg];
+    const uint64_t n_sym = (uint64_t)d.n_cmd * (4 + A.W) + d.n_lit;
+    const bool sane = n_sym <= kMaxSym && (d.payload_off & 15) == 0 &&
+                      d.payload_off + 128 + 2 * (uint64_t)d.n_words <= payload_bytes && d.level <= max_level &&
+                      !(d.n_cmd && (empty & 7u)) && !(d.n_lit && (empty & 8u));
+    if (!sane) {
+      if (lane == 0) latch(L.err, kErrCorrupt);
+      continue;
+    }
+    decode_segment(L, A, L.view0, seg, epoch, stage, lane);
+  }
+}
+
+__global__ void noalloc_status_kernel(uint32_t *status) {
+  *status = reinterpret_cast<const uint32_t *>(g_noalloc_scratch)[kCtlErr / 4];
+}
+
+std::mutex g_noalloc_mu;
+uint8_t *g_noalloc_addr[64] = {};
+
+}  // namespace
+
+extern "C" int aceapex_decode_all_noalloc(const void *d_archive, uint64_t nbytes, void *d_out, uint64_t out_cap,
+                                          uint32_t *d_status, void *stream) {
+  if (!d_archive || !d_status || nbytes < kHeaderBytes + kTablesBytes ||
+      (reinterpret_cast<uintptr_t>(d_archive) & 15))
+    return 1;  // ACEAPEX_EINVAL
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 4;  // ACEAPEX_ECUDA
+  // set-up, once per device with that device current: the device address of
+  // the scratch array (its name in host code is only a stand-in)
+  uint8_t *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void *p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return 4;
+      g_noalloc_addr[dev] = static_cast<uint8_t *>(p);
+    }
+    base = g_noalloc_addr[dev];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the header, read into host stack memory
+  uint8_t h[kHeaderBytes];
+  if (cudaMemcpyAsync(h, d_archive, kHeaderBytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return 4;
+  auto u64 = [&](int o) { uint64_t v; std::memcpy(&v, h + o, 8); return v; };
+  auto u32 = [&](int o) { uint32_t v; std::memcpy(&v, h + o, 4); return v; };
+  const uint64_t n = u64(16), n_seg = u64(40), n_deps = u64(48), n_reads = u64(56);
+  const uint32_t log2_B = h[24], log2_S = h[25], W = h[26], min_match = h[27];
+  if (std::memcmp(h, "ACEAPEX1", 8) != 0 || u32(8) != 1 || u32(12) != kHeaderBytes || h[28] != kScaleBits ||
+      h[29] != kLanes || log2_B < 2 || log2_B > 30 || log2_S != (log2_B < kMaxLog2S ? log2_B : kMaxLog2S) ||
+      W != offset_width(n) || min_match < 1)
+    return 2;  // ACEAPEX_ECORRUPT
+  const uint64_t S = uint64_t(1) << log2_S;
+  const uint64_t off_dir = u64(72), off_dep_ptr = u64(80), off_deps = u64(88), off_reads = u64(96);
+  const uint64_t off_payload = u64(104), payload_bytes = u64(112), total = u64(120);
+  if (n_seg != (n + S - 1) / S || u64(64) != kHeaderBytes || off_dir != kHeaderBytes + kTablesBytes ||
+      off_dep_ptr != round16(off_dir + 24 * n_seg) || off_deps != round16(off_dep_ptr + 8 * (n_seg + 1)) ||
+      off_reads != round16(off_deps + 4 * n_deps) || off_payload != round16(off_reads + 8 * n_reads) ||
+      total != off_payload + payload_bytes || total != nbytes)
+    return 2;
+  if (n_seg > kNoAllocMaxSegments) return 6;  // ACEAPEX_ERANGE: beyond the fixed scratch
+  if (out_cap < n || (n && !d_out)) return 6;
+  if (n == 0) return cudaMemsetAsync(d_status, 0, 4, st) == cudaSuccess ? 0 : 4;
+
+  const uint8_t *arc = static_cast<const uint8_t *>(d_archive);
+  DecodeLaunch L{};
+  DevArchive &A = L.arc0;
+  A.payload = arc + off_payload;
+  A.dir = reinterpret_cast<const SegRec *>(arc + off_dir);
+  A.lut = reinterpret_cast<const uint32_t *>(base + kNoAllocCtlBytes);
+  A.flags = reinterpret_cast<uint32_t *>(base + kNoAllocCtlBytes + kNoAllocLutBytes);
+  A.blocked = nullptr;
+  A.n = n;
+  A.D = u64(32);
+  A.log2_S = log2_S;
+  A.W = W;
+  A.min_match = min_match;
+  A.n_seg = (uint32_t)n_seg;
+  L.view0.base = static_cast<uint8_t *>(d_out);
+  L.view0.origin = 0;
+  L.view0.mask = ~uint64_t(0);
+  L.counter = reinterpret_cast<uint32_t *>(base + kCtlCounter);
+  L.epoch = reinterpret_cast<const uint32_t *>(base + kCtlEpoch);
+  L.err = reinterpret_cast<uint32_t *>(base + kCtlErr);
+  L.scratch = nullptr;
+  L.scratch_warps = kNoAllocWarps;
+  L.wait_ns = 2000000000ull;
+  noalloc_setup_kernel<<<1, 256, 0, st>>>(arc + kHeaderBytes);
+  noalloc_decode_kernel<<<kNoAllocWarps / 8, 256, 0, st>>>(L, payload_bytes, h[30]);
+  noalloc_status_kernel<<<1, 1, 0, st>>>(d_status);
+  return cudaGetLastError() == cudaSuccess ? 0 : 4;
 }
 
 }  // namespace aceapex
