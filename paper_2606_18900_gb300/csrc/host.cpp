@@ -12,7 +12,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/aceapex.h"
+#include "aceapex.h"
 #include "format.h"
 #include "kernels.h"
 
@@ -26,7 +26,7 @@ using namespace aceapex;
 
 namespace {
 
-constexpr int kBlock = 256;
+constexpr int kBlock = (int)kDecodeThreads;
 constexpr uint64_t kDefaultWaitNs = 2000000000ull;
 
 template <class T>

@@ -74,6 +74,20 @@ __device__ __forceinline__ uint8_t *at(const OutView &v, uint64_t p, uint32_t lo
   return v.base + ((p - v.origin) & v.mask);
 }
 
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // inclusive warp scan of a 32-bit value
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
 #pragma unroll
@@ -100,9 +114,42 @@ __device__ bool wait_flags(const uint32_t *flag, bool need, uint32_t epoch, uint
   }
 }
 
+// u16 little-endian at p (2-byte aligned)
+__device__ __forceinline__ uint32_t ld16(const uint8_t *p) { return *reinterpret_cast<const uint16_t *>(p); }
+__device__ __forceinline__ void st16(uint8_t *p, uint32_t v) { *reinterpret_cast<uint16_t *>(p) = (uint16_t)v; }
+
+constexpr int kViewLinear = 0, kViewRing = 1, kViewPaged = 2;
+
+// Per-warp shared table of the matches copied in one round.
+struct MatchTable {
+  uint64_t src[32];
+  uint64_t dst[32];   // absolute positions
+  uint32_t len[32];   // match length
+  uint32_t start[33]; // first 16-byte unit of each lane's match in the round; start[32] = round total
+  uint32_t pad[3];    // keeps the size a multiple of 16
+};
+
 // Decode one segment into view V and publish its ready flag.
-__device__ void decode_segment(const DecodeLaunch &L, const DevArchive &A, const OutView &V, uint32_t seg,
-                               uint32_t epoch, uint8_t *stage, int lane) {
+//
+// lut: the 4 x 4096-entry decode table (shared or global memory). sstage /
+// scap: the warp's shared-memory staging area and its size; gstage: the warp's
+// 16 KiB global staging slot, used when the command streams do not fit scap.
+// mt: the warp's shared match table; ring: the warp's 512-word shared ring.
+//
+// Phases: (1) rANS over the three command classes into staging; (2) parse,
+// scans and every rule check, rewriting each command's literal-run and
+// match-length fields in place as the inclusive literal prefix and the
+// exclusive match-length prefix; (3) rANS over the literal class, each lane
+// storing its literal straight to the output position found by its own
+// command cursor; (4) bounded waits on source segments, then match copies in
+// rounds: a round copies every pending match of a 32-command chunk whose
+// source does not overlap the output of an earlier pending match, the bytes
+// of the round spread over all lanes; (5) publish.
+template <bool kSmemLut, int kMode>
+__device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevArchive &A, const OutView &V,
+                                               uint32_t seg, uint32_t epoch, const uint32_t *lut, uint8_t *sstage,
+                                               uint32_t scap, uint8_t *gstage, MatchTable *mt, uint16_t *ring,
+                                               int lane) {
   const uint32_t log2_S = A.log2_S;
   const uint64_t seg_start = (uint64_t)seg << log2_S;
   const uint64_t rem = A.n - seg_start;
@@ -110,82 +157,171 @@ __device__ void decode_segment(const DecodeLaunch &L, const DevArchive &A, const
   const SegRec d = A.dir[seg];
   const uint32_t nc = d.n_cmd, nl = d.n_lit, nw = d.n_words, W = A.W;
   const uint32_t b1 = 2 * nc, b2 = 4 * nc, b3 = (4 + W) * nc, n_sym = b3 + nl;
-  bool ok = true;
+  uint8_t *stage = b3 <= scap ? sstage : gstage;
+  // the segment's own output is contiguous in every view
+  uint8_t *const out = at(V, seg_start, log2_S);
+  bool ok = out != nullptr;
 
   // ---------------------------------------------------------------- rANS
   const uint8_t *pl = A.payload + d.payload_off;
   uint32_t x = __ldg(reinterpret_cast<const uint32_t *>(pl) + lane);
   if (!__all_sync(kFull, x >= kRansL)) ok = false;
   const uint16_t *words = reinterpret_cast<const uint16_t *>(pl + 128);
-  uint32_t w0 = lane < nw ? __ldg(words + lane) : 0u;
-  uint32_t w1 = lane + 32 < nw ? __ldg(words + lane + 32) : 0u;
-  uint32_t base = 0, wp = 0;
+  // Renormalisation words go through a 512-word ring in shared memory, filled
+  // by cp.async in blocks of 128 words two blocks ahead of the reader, so the
+  // decode never waits on a global load between block boundaries. A lane
+  // copies a 16-byte chunk only if it starts before the segment's last word;
+  // the payload is padded to 16 bytes, so no copy leaves the archive.
+  const uint8_t *wsrc = pl + 128;
+  const uint32_t ring_s = smem_addr(ring);
+  auto fetch = [&](uint32_t blk) {
+    const uint32_t wi = blk * 128 + (uint32_t)lane * 8;
+    if (lane < 16 && wi < nw) cp_async16(ring_s + (blk & 3) * 256 + lane * 16, wsrc + (size_t)wi * 2);
+    cp_async_commit();
+  };
+  fetch(0);
+  fetch(1);
+  fetch(2);
+  fetch(3);
+  cp_async_wait<2>();
+  __syncwarp();
+  uint32_t blk = 0, wp = 0;
   const uint32_t lt = lanemask_lt();
-  for (uint32_t t0 = 0; ok && t0 < n_sym; t0 += 32) {
-    const uint32_t q = t0 + lane;
-    const bool active = q < n_sym;
-    const uint32_t cls = q < b1 ? 0u : (q < b2 ? 1u : (q < b3 ? 2u : 3u));
+  // after the step that consumed the last word of a block: reuse its slot
+  auto advance = [&]() {
+    if ((wp >> 7) != blk) {
+      blk = wp >> 7;
+      __syncwarp();
+      fetch(blk + 3);
+      cp_async_wait<2>();
+      __syncwarp();
+    }
+  };
+  // one interleaved step: lane j decodes symbol t0 + j of class cls
+  auto step = [&](uint32_t cls, bool active) -> uint32_t {
     uint32_t sym = 0;
     if (active) {
-      const uint32_t e = __ldg(A.lut + (cls << kScaleBits) + (x & (kScale - 1)));
+      const uint32_t e = lut[(cls << kScaleBits) + (x & (kScale - 1))];
       sym = e & 0xFFu;
       x = ((e >> 20) + 1u) * (x >> kScaleBits) + ((e >> 8) & 0xFFFu);
     }
     const bool need = active && x < kRansL;
     const uint32_t m = __ballot_sync(kFull, need);
-    const uint32_t k = (wp - base) + __popc(m & lt);  // < 64
-    const uint32_t lo = __shfl_sync(kFull, w0, k & 31);
-    const uint32_t hi = __shfl_sync(kFull, w1, k & 31);
-    if (need) x = (x << 16) | (k < 32 ? lo : hi);
+    if (need) x = (x << 16) | ring[(wp + __popc(m & lt)) & 511];
     wp += __popc(m);
-    if (wp - base >= 32) {
-      base += 32;
-      w0 = w1;
-      w1 = base + 32 + lane < nw ? __ldg(words + base + 32 + lane) : 0u;
-    }
-    if (active) stage[q] = (uint8_t)sym;
+    advance();
+    return sym;
+  };
+
+  // (1) command classes; the step that crosses into the literals keeps its
+  // literal symbols in `pend` until the command prefixes exist
+  uint32_t t0 = 0, pend = 0;
+  for (; ok && t0 < b3; t0 += 32) {
+    const uint32_t q = t0 + lane;
+    const uint32_t cls = q < b1 ? 0u : (q < b2 ? 1u : (q < b3 ? 2u : 3u));
+    const uint32_t sym = step(cls, q < n_sym);
+    if (q < b3) stage[q] = (uint8_t)sym;
+    else pend = sym;
   }
-  if (!__all_sync(kFull, x == kRansL) || wp != nw) ok = false;
   __syncwarp();
 
-  // ------------------------------------------------------------ commands
-  const uint64_t deadline = now_ns() + L.wait_ns;
+  // (2) parse, prefixes, checks
   const uint32_t my_level = d.level;
-  uint32_t pos = 0, litc = 0;
+  uint32_t tot_l = 0, tot_m = 0;
   for (uint32_t c0 = 0; ok && c0 < nc; c0 += 32) {
     const uint32_t c = c0 + lane;
     const bool valid = c < nc;
     uint32_t ll = 0, ml = 0;
     uint64_t src = 0;
     if (valid) {
-      ll = (uint32_t)stage[2 * c] | ((uint32_t)stage[2 * c + 1] << 8);
-      ml = ((uint32_t)stage[b1 + 2 * c] | ((uint32_t)stage[b1 + 2 * c + 1] << 8)) + A.min_match;
+      ll = ld16(stage + 2 * c);
+      ml = ld16(stage + b1 + 2 * c) + A.min_match;
       for (uint32_t b = 0; b < W; ++b) src |= (uint64_t)stage[b2 + W * c + b] << (8 * b);
     }
-    const uint32_t tot = ll + ml;
-    const uint32_t inc_t = warp_incl_scan(tot, lane), inc_l = warp_incl_scan(ll, lane);
-    const uint32_t sum_t = __shfl_sync(kFull, inc_t, 31), sum_l = __shfl_sync(kFull, inc_l, 31);
-    const uint32_t cpos = pos + inc_t - tot, clit = litc + inc_l - ll;
-    const uint64_t dst = seg_start + cpos + ll;
-    bool bad = valid && ((uint64_t)cpos + tot > out_size || (uint64_t)clit + ll > nl || src + ml > dst ||
-                         src + ml < src || (A.D && dst - src > A.D));
-    // source segments: ours, or of a lower level and present in the view
-    uint64_t q0 = 0, q1 = 0;
+    const uint32_t inc_l = warp_incl_scan(ll, lane), inc_m = warp_incl_scan(ml, lane);
+    const uint32_t lit_end = tot_l + inc_l, msum = tot_m + inc_m - ml;
+    const uint32_t cend = lit_end + msum + ml;  // end of the command in the segment
+    const uint64_t dst = seg_start + lit_end + msum;
+    bool bad = valid && ((uint64_t)cend > out_size || lit_end > nl || src + ml > dst || src + ml < src ||
+                         (A.D && dst - src > A.D));
     if (valid && !bad) {
-      q0 = src >> log2_S;
-      q1 = (src + ml - 1) >> log2_S;
+      const uint64_t q0 = src >> log2_S, q1 = (src + ml - 1) >> log2_S;
       for (uint64_t qq = q0; qq <= q1; ++qq) {
         if (qq == seg) continue;
         if (A.dir[qq].level >= my_level) bad = true;
-        if (V.page && V.page[qq] == 0xFFFFFFFFu) bad = true;
+        if (kMode == kViewPaged && V.page[qq] == 0xFFFFFFFFu) bad = true;
       }
     }
     if (__any_sync(kFull, bad)) {
       ok = false;
-      if (lane == 0) latch(L.err, kErrCorrupt);
       break;
     }
-    // bounded waits on the (at most two) source segments of each match
+    if (valid) {
+      st16(stage + 2 * c, lit_end);
+      st16(stage + b1 + 2 * c, msum);
+    }
+    tot_l += __shfl_sync(kFull, inc_l, 31);
+    tot_m += __shfl_sync(kFull, inc_m, 31);
+  }
+  if (ok && (tot_l + tot_m > out_size || out_size - tot_m != nl)) ok = false;
+  __syncwarp();
+
+  // (3) literals: lane j handles literals j, j+32, ...; its cursor (li, le,
+  // sh) is the command whose run holds its next literal (le = run end in
+  // literal numbering, sh = match bytes before that command)
+  if (ok) {
+    uint32_t li = 0, le = nc ? ld16(stage) : 0xFFFFFFFFu, sh = nc ? ld16(stage + b1) : tot_m;
+    auto place = [&](uint32_t k, uint32_t sym) {
+      while (k >= le) {
+        ++li;
+        if (li < nc) {
+          le = ld16(stage + 2 * li);
+          sh = ld16(stage + b1 + 2 * li);
+        } else {
+          le = 0xFFFFFFFFu;
+          sh = tot_m;
+        }
+      }
+      out[k + sh] = (uint8_t)sym;
+    };
+    if ((b3 & 31) && t0 - 32 + lane >= b3 && t0 - 32 + lane < n_sym) place(t0 - 32 + lane - b3, pend);
+    // full steps: every lane decodes, the class is known
+    const uint32_t *lut3 = lut + (3u << kScaleBits);
+    for (; t0 + 32 <= n_sym; t0 += 32) {
+      const uint32_t e = lut3[x & (kScale - 1)];
+      x = ((e >> 20) + 1u) * (x >> kScaleBits) + ((e >> 8) & 0xFFFu);
+      const bool need = x < kRansL;
+      const uint32_t m = __ballot_sync(kFull, need);
+      if (need) x = (x << 16) | ring[(wp + __popc(m & lt)) & 511];
+      wp += __popc(m);
+      advance();
+      place(t0 + lane - b3, e);
+    }
+    if (t0 < n_sym) {
+      const uint32_t q = t0 + lane;
+      const bool active = q < n_sym;
+      const uint32_t sym = step(3u, active);
+      if (active) place(q - b3, sym);
+      t0 += 32;
+    }
+  }
+  if (!__all_sync(kFull, x == kRansL) || wp != nw) ok = false;
+  __syncwarp();
+
+  // (4) matches
+  const uint64_t deadline = now_ns() + L.wait_ns;
+  for (uint32_t c0 = 0; ok && c0 < nc; c0 += 32) {
+    const uint32_t c = c0 + lane;
+    const bool valid = c < nc;
+    uint32_t ml = 0;
+    uint64_t src = 0, dst = ~uint64_t(0);
+    if (valid) {
+      const uint32_t msum = ld16(stage + b1 + 2 * c);
+      ml = (c + 1 < nc ? ld16(stage + b1 + 2 * c + 2) : tot_m) - msum;
+      dst = seg_start + ld16(stage + 2 * c) + msum;
+      for (uint32_t b = 0; b < W; ++b) src |= (uint64_t)stage[b2 + W * c + b] << (8 * b);
+    }
+    const uint64_t q0 = src >> log2_S, q1 = valid ? (src + ml - 1) >> log2_S : q0;
     const bool need0 = valid && q0 != seg;
     const bool need1 = valid && q1 != q0 && q1 != seg;
     if (!wait_flags(A.flags + (need0 ? q0 : 0), need0, epoch, deadline, L.err, lane) ||
@@ -193,31 +329,79 @@ __device__ void decode_segment(const DecodeLaunch &L, const DevArchive &A, const
       ok = false;
       break;
     }
+    mt->src[lane] = src;
+    mt->dst[lane] = dst;
     __syncwarp();
-    const uint32_t n_here = nc - c0 < 32 ? nc - c0 : 32;
-    for (uint32_t j = 0; j < n_here; ++j) {
-      const uint32_t jll = __shfl_sync(kFull, ll, j), jml = __shfl_sync(kFull, ml, j);
-      const uint32_t jpos = __shfl_sync(kFull, cpos, j), jlit = __shfl_sync(kFull, clit, j);
-      const uint64_t jsrc = __shfl_sync(kFull, src, j);
-      for (uint32_t k = lane; k < jll; k += 32) *at(V, seg_start + jpos + k, log2_S) = stage[b3 + jlit + k];
-      const uint64_t d0 = seg_start + jpos + jll;
-      for (uint32_t k = lane; k < jml; k += 32) *at(V, d0 + k, log2_S) = __ldcg(at(V, jsrc + k, log2_S));
+    bool pending = valid;
+    for (int round = 0;; ++round) {
+      const uint32_t pm = __ballot_sync(kFull, pending);
+      if (!pm) break;
+      // a match waits while its source overlaps the output of an earlier
+      // pending match; outputs are disjoint and ascending, so in the first
+      // round (all pending) only the last output starting before the end of
+      // the source can overlap it
+      bool haz = false;
+      if (round == 0) {
+        const uint64_t se = src + ml;
+        uint32_t j = 0;
+        bool any = false;
+#pragma unroll
+        for (int st = 16; st; st >>= 1) {
+          const uint64_t dp = __shfl_sync(kFull, dst, j + st);
+          if (dp < se) j += st;
+        }
+        const uint64_t dj = __shfl_sync(kFull, dst, j);
+        const uint32_t mj = __shfl_sync(kFull, ml, j);
+        any = dj < se && (uint32_t)lane > j;
+        haz = pending && any && dj + mj > src;
+      } else {
+        for (int j = 0; j < 32; ++j) {
+          const uint64_t dj = __shfl_sync(kFull, dst, j);
+          const uint32_t mj = __shfl_sync(kFull, ml, j);
+          if (j < lane && (pm >> j & 1u) && src < dj + mj && src + ml > dj) haz = true;
+        }
+      }
+      const bool ready = pending && !haz;
+      // units of 16 bytes: lane j copies units j, j+32, ... of the round, each
+      // with all of its loads in flight before its stores. Sources are read
+      // through L1: a 16 KiB segment never shares a sector or a line with
+      // another, and a segment is only read after its flag was acquired.
+      const uint32_t nu = ready ? (ml + 15) >> 4 : 0;
+      const uint32_t incl = warp_incl_scan(nu, lane);
+      const uint32_t total = __shfl_sync(kFull, incl, 31);
+      mt->start[lane] = incl - nu;
+      mt->len[lane] = ml;
+      if (lane == 31) mt->start[32] = incl;
       __syncwarp();
+      for (uint32_t uu = lane; uu < total; uu += 32) {
+        uint32_t m = 0;
+#pragma unroll
+        for (int st = 16; st; st >>= 1)
+          if (mt->start[m + st] <= uu) m += st;
+        const uint32_t o = (uu - mt->start[m]) << 4;
+        const uint32_t n = min(16u, mt->len[m] - o);
+        const uint64_t p = mt->src[m] + o;
+        uint8_t *to = out + (mt->dst[m] - seg_start) + o;
+        uint8_t v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          if ((uint32_t)j < n) {
+            const uint8_t *from;
+            if (kMode == kViewPaged) from = at(V, p + j, log2_S);
+            else if (kMode == kViewRing) from = V.base + ((p + j - V.origin) & V.mask);
+            else from = V.base + (p - V.origin) + j;
+            v[j] = *from;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if ((uint32_t)j < n) to[j] = v[j];
+      }
+      __syncwarp();
+      pending = pending && !ready;
     }
-    pos += sum_t;
-    litc += sum_l;
   }
-  if (ok) {
-    const uint32_t trail = out_size - pos;
-    if (pos > out_size || litc + trail != nl) {
-      ok = false;
-      if (lane == 0) latch(L.err, kErrCorrupt);
-    } else {
-      for (uint32_t k = lane; k < trail; k += 32) *at(V, seg_start + pos + k, log2_S) = stage[b3 + litc + k];
-    }
-  } else if (lane == 0 && ld_relaxed(L.err) == 0) {
-    latch(L.err, kErrCorrupt);
-  }
+  if (!ok && lane == 0 && ld_relaxed(L.err) == 0) latch(L.err, kErrCorrupt);
 
   // ------------------------------------------------------------- publish
   __threadfence();
@@ -225,11 +409,27 @@ __device__ void decode_segment(const DecodeLaunch &L, const DevArchive &A, const
   if (lane == 0 && ok && !(A.blocked && A.blocked[seg])) st_release(A.flags + seg, epoch);
 }
 
-__global__ void __launch_bounds__(256) decode_kernel(DecodeLaunch L) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t gwarp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+// Persistent decode. kSmemLut: one archive, its decode table copied to shared
+// memory once per CTA; otherwise (batches) tables are read through L1.
+// kMode: how the view maps positions (linear output, ring, or page table).
+template <bool kSmemLut, int kMode>
+__global__ void __launch_bounds__(kDecodeThreads, 1) decode_kernel(DecodeLaunch L) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t *slut = reinterpret_cast<uint32_t *>(smem);
+  uint8_t *after_lut = smem + (kSmemLut ? kLutBytes : 0);
+  MatchTable *mt = reinterpret_cast<MatchTable *>(after_lut) + wid;
+  uint16_t *ring = reinterpret_cast<uint16_t *>(after_lut + (kDecodeThreads / 32) * sizeof(MatchTable)) + wid * 512;
+  uint8_t *sstage = after_lut + (kDecodeThreads / 32) * (sizeof(MatchTable) + 1024) + (size_t)wid * kSmemStage;
+  if (kSmemLut) {
+    const uint4 *g = reinterpret_cast<const uint4 *>(L.arc0.lut);
+    uint4 *s4 = reinterpret_cast<uint4 *>(slut);
+    for (uint32_t i = threadIdx.x; i < kLutBytes / 16; i += blockDim.x) s4[i] = g[i];
+    __syncthreads();
+  }
+  const uint32_t gwarp = blockIdx.x * (blockDim.x >> 5) + wid;
   if (gwarp >= L.scratch_warps) return;
-  uint8_t *stage = L.scratch + (size_t)gwarp * kStageBytes;
+  uint8_t *gstage = L.scratch + (size_t)gwarp * kStageBytes;
   const uint32_t epoch = ld_relaxed(L.epoch);
   for (;;) {
     uint32_t idx = 0;
@@ -238,8 +438,14 @@ __global__ void __launch_bounds__(256) decode_kernel(DecodeLaunch L) {
     if (idx >= L.n_work) break;
     if (ld_relaxed(L.err) != 0) continue;  // drain the list quickly after an error
     const WorkItem w = L.work[idx];
-    if (L.arcs) decode_segment(L, L.arcs[w.arc], L.views[w.arc], w.seg, epoch, stage, lane);
-    else decode_segment(L, L.arc0, L.view0, w.seg, epoch, stage, lane);
+    if (kSmemLut)
+      decode_segment<true, kMode>(L, L.arc0, L.view0, w.seg, epoch, slut, sstage, kSmemStage, gstage, mt, ring, lane);
+    else if (L.arcs)
+      decode_segment<false, kMode>(L, L.arcs[w.arc], L.views[w.arc], w.seg, epoch, L.arcs[w.arc].lut, sstage,
+                                    kSmemStage, gstage, mt, ring, lane);
+    else
+      decode_segment<false, kMode>(L, L.arc0, L.view0, w.seg, epoch, L.arc0.lut, sstage, kSmemStage, gstage, mt,
+                                    ring, lane);
   }
 }
 
@@ -361,17 +567,37 @@ __global__ void window_crc_kernel(const uint32_t *seg_crc, uint64_t lo, uint64_t
 
 // ------------------------------------------------------------------ launchers
 
+constexpr size_t kWarpSmem = sizeof(MatchTable) + 1024 + kSmemStage;
+static_assert(sizeof(MatchTable) % 16 == 0, "keeps the rings aligned");
+constexpr size_t kSmemLutBytes = kLutBytes + (size_t)(kDecodeThreads / 32) * kWarpSmem;
+constexpr size_t kSmemNoLutBytes = (size_t)(kDecodeThreads / 32) * kWarpSmem;
+
 int decode_grid(int device, int block) {
-  int sms = 0, per_sm = 0;
+  (void)block;
+  int sms = 0, a = 0, b = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_kernel, block, 0);
+  cudaFuncSetAttribute(decode_kernel<true, kViewLinear>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kSmemLutBytes);
+  cudaFuncSetAttribute(decode_kernel<true, kViewRing>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLutBytes);
+  cudaFuncSetAttribute(decode_kernel<true, kViewPaged>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kSmemLutBytes);
+  cudaFuncSetAttribute(decode_kernel<false, kViewLinear>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kSmemNoLutBytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, decode_kernel<true, kViewLinear>, kDecodeThreads, kSmemLutBytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, decode_kernel<false, kViewLinear>, kDecodeThreads,
+                                                kSmemNoLutBytes);
+  int per_sm = a < b ? a : b;
   if (per_sm < 1) per_sm = 1;
   return sms * per_sm;
 }
 
 cudaError_t launch_decode(const DecodeLaunch &L, int grid, int block, cudaStream_t st) {
+  (void)block;
   if (L.n_work == 0) return cudaSuccess;
-  decode_kernel<<<grid, block, 0, st>>>(L);
+  if (L.arcs) decode_kernel<false, kViewLinear><<<grid, kDecodeThreads, kSmemNoLutBytes, st>>>(L);
+  else if (L.view0.page) decode_kernel<true, kViewPaged><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
+  else if (L.view0.mask != ~uint64_t(0)) decode_kernel<true, kViewRing><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
+  else decode_kernel<true, kViewLinear><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
   return cudaGetLastError();
 }
 
@@ -534,6 +760,8 @@ __global__ void __launch_bounds__(256) noalloc_decode_kernel(DecodeLaunch L, uin
   if (gwarp >= kNoAllocWarps) return;
   uint8_t *stage = g_noalloc_scratch + kNoAllocCtlBytes + kNoAllocLutBytes + kNoAllocFlagBytes +
                    (size_t)gwarp * kStageBytes;
+  __shared__ MatchTable mts[8];
+  __shared__ __align__(16) uint16_t rings[8][512];
   const uint32_t epoch = ld_relaxed(L.epoch);
   const uint32_t empty = reinterpret_cast<const uint32_t *>(g_noalloc_scratch)[kCtlEmpty / 4];
   const DevArchive &A = L.arc0;
@@ -554,7 +782,8 @@ __global__ void __launch_bounds__(256) noalloc_decode_kernel(DecodeLaunch L, uin
       if (lane == 0) latch(L.err, kErrCorrupt);
       continue;
     }
-    decode_segment(L, A, L.view0, seg, epoch, stage, lane);
+    decode_segment<false, kViewLinear>(L, A, L.view0, seg, epoch, A.lut, stage, 0, stage, &mts[threadIdx.x >> 5],
+                                       rings[threadIdx.x >> 5], lane);
   }
 }
 

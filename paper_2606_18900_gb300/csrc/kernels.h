@@ -58,7 +58,10 @@ struct DecodeLaunch {
   uint32_t scratch_warps;   // number of per-warp staging slots
 };
 
-constexpr uint32_t kStageBytes = kMaxSym;  // decoded symbols of one segment
+constexpr uint32_t kStageBytes = kMaxSym;  // global staging slot: all decoded symbols of one segment
+constexpr uint32_t kDecodeThreads = 1024;  // decode CTA: 32 warps, one CTA per SM
+constexpr uint32_t kSmemStage = 3072;      // per-warp shared staging for the command streams
+constexpr uint32_t kLutBytes = 4 * kScale * 4;
 
 struct LaunchShape {
   int grid;
