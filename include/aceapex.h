@@ -123,6 +123,20 @@ int aceapex_last_error(aceapex_archive *a, int sync, void *stream);
 int aceapex_set_wait_limit(aceapex_archive *a, uint64_t ns);
 
 /*
+ * Launch configuration of the handle's later decode calls (the autotuner's
+ * knobs): ctas = persistent CTAs (wavefront width, 1..max, one per SM at
+ * most), warps_per_cta = warps of each CTA that take work (1..32), stage_bytes
+ * = shared-memory staging per warp for the command streams (1..3072; larger
+ * segments use the warp's global staging slot). 0 selects the default (the
+ * occupancy limit, 32, 3072). Allocates the decode scratch on first use.
+ * Errors: EINVAL, ENOMEM, ECUDA. aceapex_get_launch reports the current values
+ * and the CTA limit.
+ */
+int aceapex_set_launch(aceapex_archive *a, uint32_t ctas, uint32_t warps_per_cta, uint32_t stage_bytes);
+int aceapex_get_launch(const aceapex_archive *a, uint32_t *ctas, uint32_t *max_ctas, uint32_t *warps_per_cta,
+                       uint32_t *stage_bytes);
+
+/*
  * Test hook: segments whose index is in h_segs[0..n) never publish their
  * ready flag in later launches (n = 0 clears the list). Dependent segments
  * then run into the wait limit. Lets the tests exercise ETIMEOUT without

@@ -112,6 +112,11 @@ def lib():
             L.aceapex_stream_range.argtypes = [vp, u64, u64, u64, u64, vp, vp]
             L.aceapex_decode_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), vp]
             L.aceapex_encode.argtypes = [vp, u64, u32, u32, u32, u64, u64p, u64, i32, ctypes.POINTER(vp), u64p]
+            L.aceapex_set_launch.argtypes = [vp, u32, u32, u32]
+            L.aceapex_set_launch.restype = i32
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            L.aceapex_get_launch.argtypes = [vp, u32p, u32p, u32p, u32p]
+            L.aceapex_get_launch.restype = i32
             L.aceapex_decode_all_noalloc.argtypes = [vp, u64, vp, u64, vp, vp]
             L.aceapex_decode_all_noalloc.restype = i32
             L.aceapex_free.argtypes = [vp]
@@ -259,6 +264,16 @@ class Archive:
 
     def set_wait_limit(self, ns: int):
         _check(lib().aceapex_set_wait_limit(self._h, ns), "aceapex_set_wait_limit")
+
+    def set_launch(self, ctas: int = 0, warps_per_cta: int = 0, stage_bytes: int = 0):
+        """Launch knobs of later decode calls (0 = default): persistent CTAs,
+        working warps per CTA, shared staging bytes per warp."""
+        _check(lib().aceapex_set_launch(self._h, ctas, warps_per_cta, stage_bytes), "aceapex_set_launch")
+
+    def get_launch(self) -> dict:
+        v = [ctypes.c_uint32() for _ in range(4)]
+        _check(lib().aceapex_get_launch(self._h, *[ctypes.byref(x) for x in v]), "aceapex_get_launch")
+        return dict(zip(("ctas", "max_ctas", "warps_per_cta", "stage_bytes"), [x.value for x in v]))
 
     def debug_block_segments(self, segs):
         a = np.ascontiguousarray(segs, dtype=np.uint32)

@@ -16,8 +16,11 @@
 //    lies inside the destination of an earlier match of the same segment is
 //    redirected to that match's source. The bytes are the same, the
 //    dependency set does not grow, and the decoder sees shorter chains.
+#include <sys/mman.h>
+
 #include <algorithm>
 #include <atomic>
+#include <new>
 #include <cstdlib>
 #include <cstring>
 #include <thread>
@@ -65,13 +68,42 @@ void parallel_for(uint64_t n, int threads, F &&f) {
 }
 
 
+// Uninitialised buffer of T backed by transparent huge pages when possible
+// (the chain arrays are several GB; first-touch faults on 4 KiB pages cost
+// more than the hashing). Reused across the windows of one encode call.
+template <class T>
+struct RawBuf {
+  T *p = nullptr;
+  uint64_t cap = 0;
+  void reserve(uint64_t n) {
+    if (n <= cap) return;
+    std::free(p);
+    const uint64_t bytes = ((n * sizeof(T)) + (2u << 20) - 1) & ~uint64_t((2u << 20) - 1);
+    p = static_cast<T *>(std::aligned_alloc(2u << 20, bytes));
+    if (!p) throw std::bad_alloc();
+#ifdef MADV_HUGEPAGE
+    madvise(p, bytes, MADV_HUGEPAGE);
+#endif
+    cap = n;
+  }
+  ~RawBuf() { std::free(p); }
+  T &operator[](uint64_t i) { return p[i]; }
+  const T &operator[](uint64_t i) const { return p[i]; }
+};
+
 struct Window {
   const uint8_t *in;
   uint64_t n;        // total input length
   uint64_t base;     // first position covered by the chains
   uint64_t end;      // one past the last position covered
   uint32_t hlen;
-  std::vector<uint32_t> prev;  // prev[p - base]: previous position (relative + 1) with the same hash, 0 = none
+  uint32_t sample_mask;  // positions whose hash & mask != 0 are neither indexed nor probed
+  uint64_t lim;          // positions [base, base + lim) have a full hash window
+  RawBuf<uint32_t> prev;  // prev[p - base]: previous indexed position (relative + 1) with the same hash, 0 = none
+  RawBuf<uint32_t> hv;    // hash of each position
+  RawBuf<uint32_t> idx;   // positions bucketed by hash partition
+  RawBuf<uint32_t> head;
+  bool sampled(uint64_t p) const { return p >= base && p - base < lim && (hv[p - base] & sample_mask) == 0; }
 };
 
 // hash of the first hlen (<= 16) bytes at p, kHashBits wide
@@ -83,27 +115,71 @@ inline uint32_t hash_at(const uint8_t *p, uint32_t hlen, int kHashBits) {
   return (uint32_t)((v ^ (v >> 29)) * 0xBF58476D1CE4E5B9ull >> (64 - kHashBits));
 }
 
-// Each thread owns the buckets whose top hash bits equal its index and scans
-// every position in order, so prev[] is exactly what one sequential pass
-// would build.
+// Chains equal to one sequential insertion pass, built in parallel: hash
+// every position (parallel over ranges), stably bucket the positions by the
+// top bits of their hash (counting sort, parallel over ranges), then each
+// partition's thread inserts its positions in increasing order. A partition
+// owns its head entries, so no two threads touch the same chain.
 void build_chains(Window &w, int threads) {
-  uint64_t len = w.end - w.base;
-  w.prev.assign(len, 0);
-  // about two buckets per position keeps unrelated positions off the chains
+  const uint64_t len = w.end - w.base;
   int kHashBits = 16;
   while (kHashBits < 28 && (uint64_t(1) << kHashBits) < 2 * len) ++kHashBits;
-  std::vector<uint32_t> head(size_t(1) << kHashBits, 0);
+  const uint64_t lim = (w.base + w.hlen <= w.n) ? std::min<uint64_t>(len, w.n - w.hlen + 1 - w.base) : 0;
+  w.lim = lim;
+  w.prev.reserve(len ? len : 1);
+  w.hv.reserve(lim ? lim : 1);
+  w.idx.reserve(lim ? lim : 1);
+  const uint64_t hsize = uint64_t(1) << kHashBits;
+  w.head.reserve(hsize);
   int tb = 0;
-  while ((1 << (tb + 1)) <= threads && tb < 6) ++tb;
+  while ((1 << (tb + 1)) <= threads && tb < 8) ++tb;
   const int parts = 1 << tb;
-  uint64_t lim = w.n >= w.hlen ? std::min<uint64_t>(len, w.n - w.hlen + 1 - std::min(w.base, w.n - w.hlen + 1)) : 0;
-  if (w.base + w.hlen > w.n) lim = 0;
-  parallel_for((uint64_t)parts, parts, [&](uint64_t part) {
-    for (uint64_t i = 0; i < lim; ++i) {
-      uint32_t h = hash_at(w.in + w.base + i, w.hlen, kHashBits);
-      if ((h >> (kHashBits - tb)) != part && tb) continue;
-      w.prev[i] = head[h];
-      head[h] = (uint32_t)(i + 1);
+  const int ranges = std::max(1, threads);
+  parallel_for((uint64_t)ranges, threads, [&](uint64_t r) {
+    const uint64_t hs = (hsize + ranges - 1) / ranges, a = std::min(hsize, r * hs), b = std::min(hsize, a + hs);
+    std::memset(w.head.p + a, 0, (b - a) * 4);
+    const uint64_t ps = (len + ranges - 1) / ranges, c = std::min(len, r * ps), e = std::min(len, c + ps);
+    std::memset(w.prev.p + c, 0, (e - c) * 4);
+  });
+  if (lim == 0) return;
+  const uint64_t rs = (lim + ranges - 1) / ranges;
+  std::vector<uint64_t> cnt((size_t)ranges * parts, 0);
+  const uint32_t smask = w.sample_mask;
+  parallel_for((uint64_t)ranges, threads, [&](uint64_t r) {
+    const uint64_t a = r * rs, b = std::min(lim, a + rs);
+    uint64_t *c = &cnt[r * parts];
+    for (uint64_t i = a; i < b; ++i) {
+      const uint32_t h = hash_at(w.in + w.base + i, w.hlen, kHashBits);
+      w.hv[i] = h;
+      if ((h & smask) == 0) ++c[tb ? (h >> (kHashBits - tb)) : 0];
+    }
+  });
+  // offsets: partition-major, range-minor (keeps each partition's positions ascending)
+  std::vector<uint64_t> off((size_t)ranges * parts), pstart(parts + 1, 0);
+  uint64_t acc = 0;
+  for (int p = 0; p < parts; ++p) {
+    pstart[p] = acc;
+    for (int r = 0; r < ranges; ++r) {
+      off[(size_t)r * parts + p] = acc;
+      acc += cnt[(size_t)r * parts + p];
+    }
+  }
+  pstart[parts] = acc;
+  parallel_for((uint64_t)ranges, threads, [&](uint64_t r) {
+    const uint64_t a = r * rs, b = std::min(lim, a + rs);
+    uint64_t *o = &off[r * parts];
+    for (uint64_t i = a; i < b; ++i) {
+      const uint32_t h = w.hv[i];
+      if ((h & smask) == 0) w.idx[o[tb ? (h >> (kHashBits - tb)) : 0]++] = (uint32_t)i;
+    }
+  });
+  parallel_for((uint64_t)parts, threads, [&](uint64_t p) {
+    const uint64_t a = pstart[p], b = pstart[p + 1];
+    for (uint64_t j = a; j < b; ++j) {
+      if (j + 16 < b) __builtin_prefetch(&w.head[w.hv[w.idx[j + 16]]], 1, 0);  // hide the random head access
+      const uint32_t i = w.idx[j], h = w.hv[i];
+      w.prev[i] = w.head[h];
+      w.head[h] = i + 1;
     }
   });
 }
@@ -167,11 +243,38 @@ struct Parser {
     uint64_t p = seg_start, lit_start = seg_start, ncmd = 0, mlen_sum = 0;
     bool have_next = false;
     uint64_t next_len = 0, next_src = 0;
+    const bool sparse = w.sample_mask != 0;
     while (p < seg_end) {
-      uint64_t src = 0, len;
-      if (have_next) { len = next_len; src = next_src; have_next = false; }
-      else len = find(s, Ts, p, seg_end, &src);
-      if (len >= g.min_match && p + 1 < seg_end) {
+      const uint64_t p0 = p;
+      uint64_t src = 0, len = 0;
+      if (sparse) {
+        // content-defined anchors: probe here only if this position was
+        // indexed, then extend the match backwards over the literal run
+        if (w.sampled(p)) {
+          len = find(s, Ts, p, seg_end, &src);
+          if (len) {
+            // src + len <= p - back keeps the source off the destination (R-order)
+            uint64_t back = 0;
+            const uint64_t max_back = p - (src + len);
+            while (back < max_back && p - back > lit_start && src - back > 0 &&
+                   w.in[src - back - 1] == w.in[p - back - 1]) {
+              const uint64_t q = (src - back - 1) >> g.log2_S;
+              if (q != s && ruler_target(q, g.cap) >= Ts) break;
+              ++back;
+            }
+            p -= back;
+            src -= back;
+            len += back;
+          }
+        }
+      } else if (have_next) {
+        len = next_len;
+        src = next_src;
+        have_next = false;
+      } else {
+        len = find(s, Ts, p, seg_end, &src);
+      }
+      if (!sparse && len >= g.min_match && p + 1 < seg_end) {
         next_len = find(s, Ts, p + 1, seg_end, &next_src);
         if (next_len > len) {  // one-step lazy: a literal now, the longer match next
           len = 0;
@@ -183,6 +286,7 @@ struct Parser {
         uint64_t v_now = ncmd * cs + lits + (seg_end - p);
         if (v_now + cs > kMaxSym + len) len = 0;
       }
+      if (len < g.min_match) p = p0;  // a rejected extension must not move the scan back
       if (len >= g.min_match) {
         out.push_back(Cmd{(uint32_t)(p - lit_start), (uint32_t)len, src});
         ++ncmd;
@@ -339,14 +443,20 @@ int encode_archive(const uint8_t *in, uint64_t n, uint32_t log2_B, uint32_t min_
   // ---- parse, window by window
   std::vector<std::vector<Cmd>> cmds(g.n_seg);
   const uint64_t chunk = D ? std::max<uint64_t>(uint64_t(1) << 30, g.S) : std::max<uint64_t>(n, 1);
+  Window w;
+  w.in = in;
+  w.n = n;
+  w.hlen = std::min<uint32_t>(g.min_match, 16);
+  // Long minimum matches use content-defined sampling: a position is indexed
+  // and probed only when the low bits of its hash are zero (1 in 4), which
+  // finds a match of length >= hlen + 15 with probability > 0.99 (a
+  // sampled position falls inside its first min_match - hlen + 1 starts) and
+  // cuts the indexing and probing work by four.
+  w.sample_mask = g.min_match >= w.hlen + 16 ? 3u : 0u;
   for (uint64_t a = 0; a < n; a += chunk) {
     uint64_t b = std::min(n, a + chunk);
-    Window w;
-    w.in = in;
-    w.n = n;
     w.base = D ? (a > D ? a - D : 0) : 0;
     w.end = b;
-    w.hlen = std::min<uint32_t>(g.min_match, 16);
     build_chains(w, threads);
     Parser P{g, w, 16};
     uint64_t s0 = a >> g.log2_S, s1 = (b + g.S - 1) >> g.log2_S;

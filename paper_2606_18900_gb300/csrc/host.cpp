@@ -126,7 +126,11 @@ struct aceapex_archive {
   DBuf<uint8_t> d_blocked;
   DBuf<uint8_t> d_scratch;
   uint32_t scratch_warps = 0;
-  int grid = 0;
+  int grid = 0;       // CTAs of the current launch configuration
+  int max_grid = 0;   // occupancy limit (scratch is sized for it)
+  uint32_t active_warps = kDecodeThreads / 32;
+  uint32_t stage_cap = kSmemStage;
+  uint32_t max_cmd_syms = 0;  // largest n_cmd * (4 + W) of any segment
   uint64_t wait_ns = kDefaultWaitNs;
   bool any_blocked = false;
 
@@ -142,9 +146,9 @@ struct aceapex_archive {
   DBuf<uint8_t> d_ring;
   DBuf<uint32_t> d_seg_crc;
   // batch
+  std::vector<uint8_t> batch_desc;  // host copy of what d_batch_arcs / d_batch_views hold
   DBuf<DevArchive> d_batch_arcs;
   DBuf<OutView> d_batch_views;
-  DBuf<WorkItem> d_batch_work;
   Staging stage_batch;
 
   uint32_t *err() const { return d_words.p; }
@@ -155,8 +159,7 @@ struct aceapex_archive {
     DevArchive A{};
     A.payload = d_payload.p;
     A.dir = d_dir.p;
-    A.dep_ptr = nullptr;
-    A.deps = nullptr;
+    A.order = d_order.p;
     A.lut = d_lut.p;
     A.flags = d_flags.p;
     A.blocked = any_blocked ? d_blocked.p : nullptr;
@@ -173,7 +176,6 @@ struct aceapex_archive {
     d_payload.release(); d_dir.release(); d_lut.release(); d_flags.release(); d_order.release();
     d_words.release(); d_blocked.release(); d_scratch.release(); d_page.release(); d_arena.release();
     d_work.release(); d_ring.release(); d_seg_crc.release(); d_batch_arcs.release(); d_batch_views.release();
-    d_batch_work.release();
     stage_work.release();
     stage_batch.release();
   }
@@ -237,6 +239,7 @@ int validate(const uint8_t *a, uint64_t len, aceapex_archive *A) {
     const uint64_t out_size = std::min<uint64_t>(S, h.n - s * S);
     if (r.n_lit > out_size || (uint64_t)r.n_cmd * h.min_match > out_size - r.n_lit) return ACEAPEX_ECORRUPT;
     po = round16(po + 128 + 2 * (uint64_t)r.n_words);
+    A->max_cmd_syms = std::max<uint32_t>(A->max_cmd_syms, r.n_cmd * (4 + h.W));
     n_lit += r.n_lit;
     n_cmd += r.n_cmd;
     max_lv = std::max<uint32_t>(max_lv, r.level);
@@ -309,13 +312,22 @@ void level_order(const std::vector<SegRec> &dir, const uint32_t *segs, uint64_t 
   }
 }
 
-int ensure_scratch(aceapex_archive *A) {
-  if (A->d_scratch.p) return ACEAPEX_OK;
-  A->grid = decode_grid(A->device, kBlock);
-  A->scratch_warps = (uint32_t)A->grid * (kBlock / 32);
-  if (A->d_scratch.alloc((uint64_t)A->scratch_warps * kStageBytes) != cudaSuccess) return ACEAPEX_ENOMEM;
+// Launch shape, and the per-warp global staging slots, which only segments
+// whose command streams exceed the shared stage use: they are allocated only
+// when the archive (or, for a batch, any archive) has such a segment.
+int ensure_scratch(aceapex_archive *A, uint32_t need_cmd_syms) {
+  if (!A->max_grid) {
+    A->max_grid = decode_grid(A->device, kBlock);
+    if (A->grid <= 0 || A->grid > A->max_grid) A->grid = A->max_grid;
+    A->scratch_warps = (uint32_t)A->max_grid * (kBlock / 32);
+  }
+  if (need_cmd_syms > A->stage_cap && !A->d_scratch.p) {
+    if (A->d_scratch.alloc((uint64_t)A->scratch_warps * kStageBytes) != cudaSuccess) return ACEAPEX_ENOMEM;
+  }
   return ACEAPEX_OK;
 }
+
+int ensure_scratch(aceapex_archive *A) { return ensure_scratch(A, A->max_cmd_syms); }
 
 DecodeLaunch base_launch(aceapex_archive *A) {
   DecodeLaunch L{};
@@ -326,6 +338,8 @@ DecodeLaunch base_launch(aceapex_archive *A) {
   L.scratch = A->d_scratch.p;
   L.scratch_warps = A->scratch_warps;
   L.wait_ns = A->wait_ns;
+  L.active_warps = A->active_warps;
+  L.stage_cap = A->stage_cap;
   return L;
 }
 
@@ -545,6 +559,27 @@ int aceapex_set_wait_limit(aceapex_archive *a, uint64_t ns) {
   return ACEAPEX_OK;
 }
 
+int aceapex_set_launch(aceapex_archive *a, uint32_t ctas, uint32_t warps_per_cta, uint32_t stage_bytes) {
+  if (!a || warps_per_cta > kDecodeThreads / 32 || stage_bytes > kSmemStage) return ACEAPEX_EINVAL;
+  if (cudaSetDevice(a->device) != cudaSuccess) return ACEAPEX_ECUDA;
+  int rc = ensure_scratch(a, 0);
+  if (rc) return rc;
+  a->grid = (ctas == 0 || (int)ctas > a->max_grid) ? a->max_grid : (int)ctas;
+  a->active_warps = warps_per_cta ? warps_per_cta : kDecodeThreads / 32;
+  a->stage_cap = stage_bytes ? stage_bytes : kSmemStage;
+  return ensure_scratch(a);
+}
+
+int aceapex_get_launch(const aceapex_archive *a, uint32_t *ctas, uint32_t *max_ctas, uint32_t *warps_per_cta,
+                       uint32_t *stage_bytes) {
+  if (!a || !ctas || !max_ctas || !warps_per_cta || !stage_bytes) return ACEAPEX_EINVAL;
+  *ctas = (uint32_t)a->grid;
+  *max_ctas = (uint32_t)a->max_grid;
+  *warps_per_cta = a->active_warps;
+  *stage_bytes = a->stage_cap;
+  return ACEAPEX_OK;
+}
+
 int aceapex_debug_block_segments(aceapex_archive *a, const uint32_t *segs, uint32_t n) {
   if (!a || (n && !segs)) return ACEAPEX_EINVAL;
   for (uint32_t i = 0; i < n; ++i)
@@ -648,55 +683,52 @@ int aceapex_decode_batch(aceapex_archive *const *as, int n, void *const *d_outs,
     if (!as[i] || as[i]->device != as[0]->device || (!d_outs[i] && as[i]->h.n)) return ACEAPEX_EINVAL;
   aceapex_archive *A = as[0];
   if (cudaSetDevice(A->device) != cudaSuccess) return ACEAPEX_ECUDA;
-  int rc = ensure_scratch(A);
+  uint32_t need = 0;
+  for (int i = 0; i < n; ++i) need = std::max(need, as[i]->max_cmd_syms);
+  int rc = ensure_scratch(A, need);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // merge all segments by level: counting sort over (level, archive, segment)
-  std::vector<WorkItem> work;
-  uint64_t total = 0;
-  for (int i = 0; i < n; ++i) total += as[i]->h.n_seg;
-  uint32_t cnt[257] = {};
+  // largest archives first, so the last CTAs to finish hold small ones
+  std::vector<int> perm;
   for (int i = 0; i < n; ++i)
-    for (const SegRec &r : as[i]->dir) cnt[r.level + 1]++;
-  for (int l = 0; l < 256; ++l) cnt[l + 1] += cnt[l];
-  work.resize(total);
-  for (int i = 0; i < n; ++i)
-    for (uint64_t s = 0; s < as[i]->h.n_seg; ++s) work[cnt[as[i]->dir[s].level]++] = WorkItem{(uint32_t)i, (uint32_t)s};
-  if (total == 0) return ACEAPEX_OK;
-  std::vector<DevArchive> arcs(n);
-  std::vector<OutView> views(n);
-  for (int i = 0; i < n; ++i) {
-    arcs[i] = as[i]->dev();
-    views[i] = linear_view(static_cast<uint8_t *>(d_outs[i]), 0);
+    if (as[i]->h.n_seg) perm.push_back(i);
+  std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return as[x]->h.n_seg > as[y]->h.n_seg; });
+  const uint32_t m = (uint32_t)perm.size();
+  if (m == 0) return ACEAPEX_OK;
+  std::vector<DevArchive> arcs(m);
+  std::vector<OutView> views(m);
+  for (uint32_t k = 0; k < m; ++k) {
+    arcs[k] = as[perm[k]]->dev();
+    views[k] = linear_view(static_cast<uint8_t *>(d_outs[perm[k]]), 0);
   }
-  const uint64_t bytes = sizeof(DevArchive) * n + sizeof(OutView) * n + sizeof(WorkItem) * total;
-  if (A->d_batch_work.n < total || A->d_batch_arcs.n < (uint64_t)n) {
-    cudaStreamSynchronize(st);
-    if (A->d_batch_work.alloc(total) != cudaSuccess || A->d_batch_arcs.alloc(n) != cudaSuccess ||
-        A->d_batch_views.alloc(n) != cudaSuccess)
-      return ACEAPEX_ENOMEM;
+  // the device copy of the batch description is reused while it is unchanged,
+  // so a repeated call (or its capture into a CUDA graph) issues kernels only
+  const uint64_t bytes = (sizeof(DevArchive) + sizeof(OutView)) * m;
+  std::vector<uint8_t> desc(bytes);
+  std::memcpy(desc.data(), arcs.data(), sizeof(DevArchive) * m);
+  std::memcpy(desc.data() + sizeof(DevArchive) * m, views.data(), sizeof(OutView) * m);
+  if (desc != A->batch_desc) {
+    if (A->d_batch_arcs.n < m) {
+      cudaStreamSynchronize(st);
+      if (A->d_batch_arcs.alloc(m) != cudaSuccess || A->d_batch_views.alloc(m) != cudaSuccess) return ACEAPEX_ENOMEM;
+    }
+    if (A->stage_batch.reserve(bytes) != cudaSuccess) return ACEAPEX_ENOMEM;
+    uint8_t *p = static_cast<uint8_t *>(A->stage_batch.p);
+    std::memcpy(p, desc.data(), bytes);
+    cudaError_t e = cudaMemcpyAsync(A->d_batch_arcs.p, p, sizeof(DevArchive) * m, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(A->d_batch_views.p, p + sizeof(DevArchive) * m, sizeof(OutView) * m,
+                          cudaMemcpyHostToDevice, st);
+    A->stage_batch.mark(st);
+    if (e != cudaSuccess) return ACEAPEX_ECUDA;
+    A->batch_desc.swap(desc);
   }
-  if (A->stage_batch.reserve(bytes) != cudaSuccess) return ACEAPEX_ENOMEM;
-  uint8_t *p = static_cast<uint8_t *>(A->stage_batch.p);
-  std::memcpy(p, arcs.data(), sizeof(DevArchive) * n);
-  std::memcpy(p + sizeof(DevArchive) * n, views.data(), sizeof(OutView) * n);
-  std::memcpy(p + (sizeof(DevArchive) + sizeof(OutView)) * n, work.data(), sizeof(WorkItem) * total);
-  cudaError_t e = cudaMemcpyAsync(A->d_batch_arcs.p, p, sizeof(DevArchive) * n, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(A->d_batch_views.p, p + sizeof(DevArchive) * n, sizeof(OutView) * n, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(A->d_batch_work.p, p + (sizeof(DevArchive) + sizeof(OutView)) * n, sizeof(WorkItem) * total,
-                        cudaMemcpyHostToDevice, st);
-  A->stage_batch.mark(st);
-  if (e != cudaSuccess) return ACEAPEX_ECUDA;
   uint32_t *ge = global_epoch(A->device);
   if (!ge || launch_begin(ge, A->epoch(), A->counter(), st) != cudaSuccess) return ACEAPEX_ECUDA;
   DecodeLaunch L = base_launch(A);
   L.arcs = A->d_batch_arcs.p;
   L.views = A->d_batch_views.p;
-  L.work = A->d_batch_work.p;
-  L.n_work = (uint32_t)total;
-  return cuda_status(launch_decode(L, A->grid, kBlock, st));
+  return cuda_status(launch_batch(L, m, A->grid, st));
 }
 
 int aceapex_encode(const void *h_in, uint64_t n, uint32_t log2_B, uint32_t min_match, uint32_t max_level,

@@ -409,26 +409,26 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
   if (lane == 0 && ok && !(A.blocked && A.blocked[seg])) st_release(A.flags + seg, epoch);
 }
 
-// Persistent decode. kSmemLut: one archive, its decode table copied to shared
-// memory once per CTA; otherwise (batches) tables are read through L1.
+// Persistent decode of one archive: its decode table is copied to shared
+// memory once per CTA, and every warp takes the next work item.
 // kMode: how the view maps positions (linear output, ring, or page table).
-template <bool kSmemLut, int kMode>
+template <int kMode>
 __global__ void __launch_bounds__(kDecodeThreads, 1) decode_kernel(DecodeLaunch L) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t *slut = reinterpret_cast<uint32_t *>(smem);
-  uint8_t *after_lut = smem + (kSmemLut ? kLutBytes : 0);
+  uint8_t *after_lut = smem + kLutBytes;
   MatchTable *mt = reinterpret_cast<MatchTable *>(after_lut) + wid;
   uint16_t *ring = reinterpret_cast<uint16_t *>(after_lut + (kDecodeThreads / 32) * sizeof(MatchTable)) + wid * 512;
   uint8_t *sstage = after_lut + (kDecodeThreads / 32) * (sizeof(MatchTable) + 1024) + (size_t)wid * kSmemStage;
-  if (kSmemLut) {
+  {
     const uint4 *g = reinterpret_cast<const uint4 *>(L.arc0.lut);
     uint4 *s4 = reinterpret_cast<uint4 *>(slut);
     for (uint32_t i = threadIdx.x; i < kLutBytes / 16; i += blockDim.x) s4[i] = g[i];
     __syncthreads();
   }
   const uint32_t gwarp = blockIdx.x * (blockDim.x >> 5) + wid;
-  if (gwarp >= L.scratch_warps) return;
+  if (gwarp >= L.scratch_warps || (uint32_t)wid >= L.active_warps) return;
   uint8_t *gstage = L.scratch + (size_t)gwarp * kStageBytes;
   const uint32_t epoch = ld_relaxed(L.epoch);
   for (;;) {
@@ -437,15 +437,54 @@ __global__ void __launch_bounds__(kDecodeThreads, 1) decode_kernel(DecodeLaunch 
     idx = __shfl_sync(kFull, idx, 0);
     if (idx >= L.n_work) break;
     if (ld_relaxed(L.err) != 0) continue;  // drain the list quickly after an error
-    const WorkItem w = L.work[idx];
-    if (kSmemLut)
-      decode_segment<true, kMode>(L, L.arc0, L.view0, w.seg, epoch, slut, sstage, kSmemStage, gstage, mt, ring, lane);
-    else if (L.arcs)
-      decode_segment<false, kMode>(L, L.arcs[w.arc], L.views[w.arc], w.seg, epoch, L.arcs[w.arc].lut, sstage,
-                                    kSmemStage, gstage, mt, ring, lane);
-    else
-      decode_segment<false, kMode>(L, L.arc0, L.view0, w.seg, epoch, L.arc0.lut, sstage, kSmemStage, gstage, mt,
-                                    ring, lane);
+    decode_segment<true, kMode>(L, L.arc0, L.view0, L.work[idx].seg, epoch, slut, sstage, L.stage_cap, gstage, mt,
+                                ring, lane);
+  }
+}
+
+// Batch decode, one archive per CTA at a time (see launch_batch).
+__global__ void __launch_bounds__(kDecodeThreads, 1) batch_kernel(DecodeLaunch L, uint32_t n_arcs) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ uint32_t s_arc, s_next;
+  __shared__ DevArchive s_A;
+  __shared__ OutView s_V;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t *slut = reinterpret_cast<uint32_t *>(smem);
+  uint8_t *after_lut = smem + kLutBytes;
+  MatchTable *mt = reinterpret_cast<MatchTable *>(after_lut) + wid;
+  uint16_t *ring = reinterpret_cast<uint16_t *>(after_lut + (kDecodeThreads / 32) * sizeof(MatchTable)) + wid * 512;
+  uint8_t *sstage = after_lut + (kDecodeThreads / 32) * (sizeof(MatchTable) + 1024) + (size_t)wid * kSmemStage;
+  const uint32_t gwarp = blockIdx.x * (blockDim.x >> 5) + wid;
+  uint8_t *gstage = L.scratch + (size_t)gwarp * kStageBytes;
+  const uint32_t epoch = ld_relaxed(L.epoch);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_arc = atomicAdd(L.counter, 1u);
+      s_next = 0;
+    }
+    __syncthreads();
+    const uint32_t a = s_arc;
+    if (a >= n_arcs) break;
+    if (threadIdx.x == 0) {
+      s_A = L.arcs[a];
+      s_V = L.views[a];
+    }
+    __syncthreads();
+    const DevArchive &A = s_A;
+    const uint4 *g = reinterpret_cast<const uint4 *>(A.lut);
+    uint4 *s4 = reinterpret_cast<uint4 *>(slut);
+    for (uint32_t i = threadIdx.x; i < kLutBytes / 16; i += blockDim.x) s4[i] = g[i];
+    __syncthreads();
+    for (; (uint32_t)wid < L.active_warps;) {
+      uint32_t idx = 0;
+      if (lane == 0) idx = atomicAdd(&s_next, 1u);
+      idx = __shfl_sync(kFull, idx, 0);
+      if (idx >= A.n_seg) break;
+      if (ld_relaxed(L.err) != 0) continue;
+      decode_segment<true, kViewLinear>(L, A, s_V, A.order[idx].seg, epoch, slut, sstage, L.stage_cap, gstage, mt,
+                                        ring, lane);
+    }
+    __syncthreads();  // the table is replaced only after every warp left this archive
   }
 }
 
@@ -570,22 +609,19 @@ __global__ void window_crc_kernel(const uint32_t *seg_crc, uint64_t lo, uint64_t
 constexpr size_t kWarpSmem = sizeof(MatchTable) + 1024 + kSmemStage;
 static_assert(sizeof(MatchTable) % 16 == 0, "keeps the rings aligned");
 constexpr size_t kSmemLutBytes = kLutBytes + (size_t)(kDecodeThreads / 32) * kWarpSmem;
-constexpr size_t kSmemNoLutBytes = (size_t)(kDecodeThreads / 32) * kWarpSmem;
 
 int decode_grid(int device, int block) {
   (void)block;
   int sms = 0, a = 0, b = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  cudaFuncSetAttribute(decode_kernel<true, kViewLinear>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(decode_kernel<kViewLinear>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)kSmemLutBytes);
-  cudaFuncSetAttribute(decode_kernel<true, kViewRing>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLutBytes);
-  cudaFuncSetAttribute(decode_kernel<true, kViewPaged>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(decode_kernel<kViewRing>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLutBytes);
+  cudaFuncSetAttribute(decode_kernel<kViewPaged>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)kSmemLutBytes);
-  cudaFuncSetAttribute(decode_kernel<false, kViewLinear>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)kSmemNoLutBytes);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, decode_kernel<true, kViewLinear>, kDecodeThreads, kSmemLutBytes);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, decode_kernel<false, kViewLinear>, kDecodeThreads,
-                                                kSmemNoLutBytes);
+  cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLutBytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, decode_kernel<kViewLinear>, kDecodeThreads, kSmemLutBytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_kernel, kDecodeThreads, kSmemLutBytes);
   int per_sm = a < b ? a : b;
   if (per_sm < 1) per_sm = 1;
   return sms * per_sm;
@@ -594,10 +630,16 @@ int decode_grid(int device, int block) {
 cudaError_t launch_decode(const DecodeLaunch &L, int grid, int block, cudaStream_t st) {
   (void)block;
   if (L.n_work == 0) return cudaSuccess;
-  if (L.arcs) decode_kernel<false, kViewLinear><<<grid, kDecodeThreads, kSmemNoLutBytes, st>>>(L);
-  else if (L.view0.page) decode_kernel<true, kViewPaged><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
-  else if (L.view0.mask != ~uint64_t(0)) decode_kernel<true, kViewRing><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
-  else decode_kernel<true, kViewLinear><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
+  if (L.view0.page) decode_kernel<kViewPaged><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
+  else if (L.view0.mask != ~uint64_t(0)) decode_kernel<kViewRing><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
+  else decode_kernel<kViewLinear><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const DecodeLaunch &L, uint32_t n_arcs, int grid, cudaStream_t st) {
+  if (n_arcs == 0) return cudaSuccess;
+  cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLutBytes);
+  batch_kernel<<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L, n_arcs);
   return cudaGetLastError();
 }
 

@@ -12,12 +12,17 @@ namespace aceapex {
 constexpr uint32_t kErrCorrupt = 2;
 constexpr uint32_t kErrTimeout = 5;
 
+// A unit of work: archive index (batch) and segment.
+struct WorkItem {
+  uint32_t arc;
+  uint32_t seg;
+};
+
 // One archive as the kernels see it (all pointers are device pointers).
 struct DevArchive {
   const uint8_t *payload;   // payload section (segment payloads, 16-byte aligned)
   const SegRec *dir;        // segment directory
-  const uint64_t *dep_ptr;  // n_seg + 1
-  const uint32_t *deps;     // dependency lists
+  const WorkItem *order;    // all segments in level order
   const uint32_t *lut;      // 4 classes x 4096 slots: sym | bias << 8 | (freq - 1) << 20
   uint32_t *flags;          // per-segment ready flag (= epoch when complete)
   const uint8_t *blocked;   // test hook: per-segment "never publish" bytes, or nullptr
@@ -37,12 +42,6 @@ struct OutView {
   uint8_t *slot_base;
 };
 
-// A unit of work: archive index (batch) and segment.
-struct WorkItem {
-  uint32_t arc;
-  uint32_t seg;
-};
-
 struct DecodeLaunch {
   DevArchive arc0;          // single-archive launches
   OutView view0;
@@ -56,6 +55,8 @@ struct DecodeLaunch {
   uint8_t *scratch;         // per-warp staging, kStageBytes each
   uint64_t wait_ns;         // dependency wait limit
   uint32_t scratch_warps;   // number of per-warp staging slots
+  uint32_t active_warps;    // warps per CTA that take work (<= kDecodeThreads / 32)
+  uint32_t stage_cap;       // bytes of a warp's shared staging to use (<= kSmemStage)
 };
 
 constexpr uint32_t kStageBytes = kMaxSym;  // global staging slot: all decoded symbols of one segment
@@ -81,6 +82,11 @@ cudaError_t launch_clear_pages(uint32_t *page, const WorkItem *work, uint32_t n,
 
 // copy [lo, hi) from view src to view dst (both addressed by absolute position)
 cudaError_t launch_copy_view(OutView src, OutView dst, uint32_t log2_S, uint64_t lo, uint64_t hi, cudaStream_t st);
+
+// Batch decode: each CTA takes whole archives (L.arcs[0..n_arcs), largest
+// first) and decodes each archive's segments in its level order with the
+// archive's decode table in shared memory. L.work is unused.
+cudaError_t launch_batch(const DecodeLaunch &L, uint32_t n_arcs, int grid, cudaStream_t st);
 
 // Occupancy-derived grid for the decode kernel.
 int decode_grid(int device, int block);

@@ -30,7 +30,7 @@ def build(force: bool = False) -> str:
     """Compile libsynth.so next to its source (host C, portable flags)."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -51,6 +51,8 @@ def _load():
             lib.synth_fasta_free.argtypes = [ctypes.c_void_p]
             lib.synth_fasta_read.argtypes = [ctypes.c_void_p, u8p, u64]
             lib.synth_fasta_read.restype = u64
+            lib.synth_fasta_fill.argtypes = [u64, u64, u64, ctypes.c_int, ctypes.c_int, u8p]
+            lib.synth_fasta_fill.restype = ctypes.c_int
             lib.synth_loguniform_sizes.argtypes = [u64, u64, u64, ctypes.c_double, ctypes.c_double, u64p]
             lib.synth_uniform.argtypes = [u64, u64, u64, u64, u64p]
             lib.synth_bytes.argtypes = [u64, u64, u64, u8p, ctypes.c_int, u8p]
@@ -117,15 +119,20 @@ def batch_sizes(n: int = 4096, seed: int = 3, lo: int = 16384, hi: int = 1 << 24
     return out
 
 
-def batch_fastq(sizes, seed: int = 3, ref_len: int = 50_000_000):
+def batch_fastq(sizes, seed: int = 3, ref_len: int = 50_000_000, threads: int = 0):
     """One paired-end FASTQ per size, each cut to exactly its size; all share
-    one reference drawn from ``seed`` and draw reads from seed (seed, i)."""
+    one reference drawn from ``seed`` and draw reads from seed (seed, 1000 + i).
+    Archives are generated in parallel threads (the C generator releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     ref = reference(seed, 0, ref_len, repeat_frac=0.05, n_families=50)
-    outs = []
-    for i, s in enumerate(sizes):
-        d, _ = fastq(ref, seed, 1000 + i, paired=True, max_bytes=int(s), truncate=True)
-        outs.append(d.copy())
-    return outs
+
+    def one(i):
+        d, _ = fastq(ref, seed, 1000 + i, paired=True, max_bytes=int(sizes[i]), truncate=True)
+        return d.copy()
+
+    with ThreadPoolExecutor(threads or (os.cpu_count() or 1)) as ex:
+        return list(ex.map(one, range(len(sizes))))
 
 
 class FastaStream:
@@ -158,12 +165,14 @@ class FastaStream:
             pass
 
 
-def fasta(total_bytes: int, seed: int = 4, n_chrom: int = 24) -> np.ndarray:
-    s = FastaStream(total_bytes, seed, n_chrom)
+def fasta(total_bytes: int, seed: int = 4, n_chrom: int = 24, threads: int = 0) -> np.ndarray:
+    """The whole genome file; chromosomes are generated in parallel (same
+    bytes as FastaStream)."""
+    lib = _load()
     out = np.empty(total_bytes, dtype=np.uint8)
-    k = s.read_into(out)
-    s.close()
-    assert k == total_bytes
+    threads = threads or min(64, os.cpu_count() or 1)
+    if lib.synth_fasta_fill(seed, 0, total_bytes, n_chrom, threads, _p8(out)) != 0:
+        raise ValueError("bad FASTA parameters")
     return out
 
 

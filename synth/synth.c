@@ -13,6 +13,7 @@
  * on every host. Log-uniform draws use exp2() from the C library.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -285,155 +286,225 @@ int64_t synth_fastq(const uint8_t *ref, uint64_t ref_len, uint64_t seed_a, uint6
 /* ------------------------------------------------------------------ FASTA */
 
 /*
- * Streaming FASTA genome: n_chrom records ">chrK\n" + 60-column lines.
- * Chromosome lengths are 2.5e9 - s(2.5e9 - u_k), u_k ~ U[0.5e9, 2.5e9], with
- * s fitted so the file totals total_bytes (proportional scaling u_k * t when
- * the fit leaves [0, 1]). The stream stops at exactly total_bytes (the last
- * chromosome absorbs the rounding). Sequence: uppercase unique stretches
- * alternate with lowercase copies of repeat families (diverged 5-20%, 1%
- * indels) so that about 45% of bases are repeat copies; each chromosome holds
- * Poisson(4) runs of 'N' of log-uniform length in [1e4, 3e6].
+ * FASTA genome of exactly total_bytes bytes: n_chrom records ">chrK\n" +
+ * 60-column lines (a newline after every full line and after the last bases
+ * of a chromosome). Chromosome lengths are 2.5e9 - s(2.5e9 - u_k), u_k ~
+ * U[0.5e9, 2.5e9], with s fitted so the file totals total_bytes (u_k scaled
+ * proportionally when the fit leaves [0, 1]); the last chromosome runs until
+ * the file reaches total_bytes. Sequence: uppercase unique stretches
+ * alternate with lowercase copies of 500 repeat families (diverged 5-20%,
+ * 1% indels), about 45% of bases in repeats; each chromosome holds Poisson(4)
+ * runs of 'N' of log-uniform length in [1e4, 3e6].
+ *
+ * Randomness: one stream draws the families and lengths; chromosome k has a
+ * stream of its own (seed_b + 1 + k), so chromosomes can be generated in
+ * parallel and the streaming reader yields the same bytes.
  */
 #define FA_MAX_CHROM 64
 #define FA_NFAM 500
 #define FA_MAX_NRUN 32
 
 typedef struct {
-  rng_t r;
-  uint64_t total, emitted;
-  int n_chrom, chrom;           /* current chromosome (0-based) */
-  uint64_t clen[FA_MAX_CHROM];  /* bases per chromosome */
-  uint64_t pos;                 /* bases emitted in current chromosome */
-  int col;                      /* column in current line */
-  char hdr[32];
-  int hdr_len, hdr_at;          /* pending header bytes */
+  uint64_t total;
+  int n_chrom;
+  uint64_t clen[FA_MAX_CHROM];   /* bases per chromosome (last: unbounded) */
+  uint64_t cbytes[FA_MAX_CHROM]; /* bytes per chromosome record (last: rest of the file) */
+  uint64_t coff[FA_MAX_CHROM];   /* byte offset of each record */
   uint8_t *fam[FA_NFAM];
   uint32_t flen[FA_NFAM];
-  /* N runs of the current chromosome */
+  uint64_t seed_a, seed_b;
+} fa_spec_t;
+
+typedef struct {
+  const fa_spec_t *sp;
+  rng_t r;
+  int k;
+  uint64_t pos, emitted, limit; /* bases emitted, bytes emitted, byte limit of this record */
+  int col;
+  char hdr[32];
+  int hdr_len, hdr_at;
   uint64_t nrun_start[FA_MAX_NRUN], nrun_len[FA_MAX_NRUN];
   int n_nrun, nrun_at;
-  /* current feature: 0 unique, 1 repeat copy, 2 N run */
-  int feat;
-  uint64_t feat_left;           /* bases left (unique / N) */
+  int feat; /* 0 unique, 1 repeat copy, 2 N run */
+  uint64_t feat_left;
   uint32_t rep_fam, rep_at, rep_div_ppm;
-  int need_newline_at_end;      /* pending '\n' after the last base of a chromosome */
-} fasta_t;
+  int ended;
+} fa_chrom_t;
 
-static void fa_begin_chrom(fasta_t *g) {
-  int k = g->chrom;
+static uint64_t fa_record_bytes(int k, uint64_t L) {
+  uint64_t h = (k + 1 < 10) ? 6 : 7;
+  return h + L + (L + 59) / 60;
+}
+
+static void fa_chrom_init(fa_chrom_t *c, const fa_spec_t *sp, int k) {
+  memset(c, 0, sizeof(*c));
+  c->sp = sp;
+  c->k = k;
+  rng_seed(&c->r, sp->seed_a ^ 0xFA5Aull, sp->seed_b + 1 + (uint64_t)k);
+  c->limit = sp->cbytes[k];
   int n = 0;
-  g->hdr[n++] = '>'; g->hdr[n++] = 'c'; g->hdr[n++] = 'h'; g->hdr[n++] = 'r';
+  c->hdr[n++] = '>'; c->hdr[n++] = 'c'; c->hdr[n++] = 'h'; c->hdr[n++] = 'r';
   char t[16];
   int m = 0, v = k + 1;
   do { t[m++] = (char)('0' + v % 10); v /= 10; } while (v);
-  while (m) g->hdr[n++] = t[--m];
-  g->hdr[n++] = '\n';
-  g->hdr_len = n; g->hdr_at = 0;
-  g->pos = 0; g->col = 0;
+  while (m) c->hdr[n++] = t[--m];
+  c->hdr[n++] = '\n';
+  c->hdr_len = n;
   /* N runs: Poisson(4) count, uniform starts, log-uniform lengths */
   double lim = exp(-4.0), p = 1.0;
   int cnt = 0;
-  for (;;) { p *= rng_unit(&g->r); if (p <= lim) break; ++cnt; }
+  for (;;) { p *= rng_unit(&c->r); if (p <= lim) break; ++cnt; }
   if (cnt > FA_MAX_NRUN) cnt = FA_MAX_NRUN;
-  uint64_t L = g->clen[k];
+  uint64_t L = sp->clen[k];
+  uint64_t span = (k == sp->n_chrom - 1) ? (sp->cbytes[k] * 60 / 61) : L;
   for (int i = 0; i < cnt; ++i) {
-    g->nrun_start[i] = L ? rng_below(&g->r, L) : 0;
-    g->nrun_len[i] = rng_loguniform(&g->r, 1e4, 3e6);
+    c->nrun_start[i] = span ? rng_below(&c->r, span) : 0;
+    c->nrun_len[i] = rng_loguniform(&c->r, 1e4, 3e6);
   }
-  /* sort starts (insertion sort, cnt <= 32) */
   for (int i = 1; i < cnt; ++i) {
-    uint64_t s = g->nrun_start[i], l = g->nrun_len[i];
+    uint64_t s0 = c->nrun_start[i], l0 = c->nrun_len[i];
     int j = i - 1;
-    while (j >= 0 && g->nrun_start[j] > s) { g->nrun_start[j + 1] = g->nrun_start[j]; g->nrun_len[j + 1] = g->nrun_len[j]; --j; }
-    g->nrun_start[j + 1] = s; g->nrun_len[j + 1] = l;
+    while (j >= 0 && c->nrun_start[j] > s0) { c->nrun_start[j + 1] = c->nrun_start[j]; c->nrun_len[j + 1] = c->nrun_len[j]; --j; }
+    c->nrun_start[j + 1] = s0; c->nrun_len[j + 1] = l0;
   }
-  g->n_nrun = cnt; g->nrun_at = 0;
-  g->feat = 0; g->feat_left = 1 + rng_below(&g->r, 2 * 2326);
+  c->n_nrun = cnt;
+  c->feat = 0;
+  c->feat_left = 1 + rng_below(&c->r, 2 * 2326);
 }
 
 /* pick the next feature: a due N run, else a repeat copy after a unique
  * stretch and a unique stretch after anything else (mean unique length 2326
  * against a mean repeat length of ~1900 gives a ~45% repeat share) */
-static void fa_next_feature(fasta_t *g, int after_unique) {
-  if (g->nrun_at < g->n_nrun && g->nrun_start[g->nrun_at] <= g->pos) {
-    g->feat = 2;
-    g->feat_left = g->nrun_len[g->nrun_at++];
+static void fa_next_feature(fa_chrom_t *c, int after_unique) {
+  if (c->nrun_at < c->n_nrun && c->nrun_start[c->nrun_at] <= c->pos) {
+    c->feat = 2;
+    c->feat_left = c->nrun_len[c->nrun_at++];
     return;
   }
   if (after_unique) {
-    g->feat = 1;
-    g->rep_fam = (uint32_t)rng_below(&g->r, FA_NFAM);
-    g->rep_at = 0;
-    g->rep_div_ppm = 50000 + (uint32_t)rng_below(&g->r, 150001);
+    c->feat = 1;
+    c->rep_fam = (uint32_t)rng_below(&c->r, FA_NFAM);
+    c->rep_at = 0;
+    c->rep_div_ppm = 50000 + (uint32_t)rng_below(&c->r, 150001);
     return;
   }
-  g->feat = 0;
-  g->feat_left = 1 + rng_below(&g->r, 2 * 2326);
+  c->feat = 0;
+  c->feat_left = 1 + rng_below(&c->r, 2 * 2326);
 }
 
-/* next sequence base of the current chromosome */
-static uint8_t fa_base(fasta_t *g) {
+static uint8_t fa_base(fa_chrom_t *c) {
+  const fa_spec_t *sp = c->sp;
   for (;;) {
-    if (g->feat == 2) {
-      if (g->feat_left) { --g->feat_left; return 'N'; }
-      fa_next_feature(g, 0);
+    if (c->feat == 2) {
+      if (c->feat_left) { --c->feat_left; return 'N'; }
+      fa_next_feature(c, 0);
       continue;
     }
-    if (g->feat == 1) {
-      uint32_t f = g->rep_fam;
-      if (g->rep_at >= g->flen[f]) { fa_next_feature(g, 0); continue; }
-      uint64_t u = rng_below(&g->r, 1000000);
-      if (u < 5000) { ++g->rep_at; continue; }                            /* deletion */
-      if (u < 10000) return (uint8_t)(BASES[rng_next(&g->r) >> 62] | 0x20); /* insertion */
-      uint8_t b = g->fam[f][g->rep_at++];
-      if (u < 10000 + g->rep_div_ppm) {
-        int k = (int)(base_idx(b) + 1 + rng_below(&g->r, 3)) & 3;
+    if (c->feat == 1) {
+      uint32_t f = c->rep_fam;
+      if (c->rep_at >= sp->flen[f]) { fa_next_feature(c, 0); continue; }
+      uint64_t u = rng_below(&c->r, 1000000);
+      if (u < 5000) { ++c->rep_at; continue; }                            /* deletion */
+      if (u < 10000) return (uint8_t)(BASES[rng_next(&c->r) >> 62] | 0x20); /* insertion */
+      uint8_t b = sp->fam[f][c->rep_at++];
+      if (u < 10000 + c->rep_div_ppm) {
+        int k = (int)(base_idx(b) + 1 + rng_below(&c->r, 3)) & 3;
         b = (uint8_t)BASES[k];
       }
       return (uint8_t)(b | 0x20);
     }
-    if (g->nrun_at < g->n_nrun && g->nrun_start[g->nrun_at] <= g->pos) { fa_next_feature(g, 0); continue; }
-    if (g->feat_left == 0) { fa_next_feature(g, 1); continue; }
-    --g->feat_left;
-    return (uint8_t)BASES[rng_next(&g->r) >> 62];
+    if (c->nrun_at < c->n_nrun && c->nrun_start[c->nrun_at] <= c->pos) { fa_next_feature(c, 0); continue; }
+    if (c->feat_left == 0) { fa_next_feature(c, 1); continue; }
+    --c->feat_left;
+    return (uint8_t)BASES[rng_next(&c->r) >> 62];
   }
 }
 
-void *synth_fasta_new(uint64_t seed_a, uint64_t seed_b, uint64_t total_bytes, int n_chrom) {
-  if (n_chrom < 1 || n_chrom > FA_MAX_CHROM) return NULL;
-  fasta_t *g = (fasta_t *)calloc(1, sizeof(fasta_t));
-  if (!g) return NULL;
-  rng_seed(&g->r, seed_a ^ 0xFA5Aull, seed_b);
-  g->total = total_bytes;
-  g->n_chrom = n_chrom;
-  for (int f = 0; f < FA_NFAM; ++f) {
-    g->flen[f] = (uint32_t)rng_loguniform(&g->r, 300.0, 6000.0);
-    g->fam[f] = (uint8_t *)malloc(g->flen[f]);
-    for (uint32_t i = 0; i < g->flen[f]; ++i) g->fam[f][i] = (uint8_t)BASES[rng_next(&g->r) >> 62];
+/* next n bytes of chromosome record c (fewer at its end) */
+static uint64_t fa_chrom_read(fa_chrom_t *c, uint8_t *out, uint64_t n) {
+  uint64_t w = 0;
+  const uint64_t L = c->sp->clen[c->k];
+  while (w < n && c->emitted < c->limit) {
+    if (c->hdr_at < c->hdr_len) { out[w++] = (uint8_t)c->hdr[c->hdr_at++]; ++c->emitted; continue; }
+    if (c->col == 60 || (c->pos == L && c->col > 0)) {
+      out[w++] = '\n'; ++c->emitted; c->col = 0;
+      continue;
+    }
+    out[w++] = fa_base(c); ++c->emitted;
+    ++c->col; ++c->pos;
   }
-  /* chromosome lengths: bases ~= (total - headers) * 60/61 */
+  return w;
+}
+
+static fa_spec_t *fa_spec_new(uint64_t seed_a, uint64_t seed_b, uint64_t total_bytes, int n_chrom) {
+  if (n_chrom < 1 || n_chrom > FA_MAX_CHROM) return NULL;
+  fa_spec_t *sp = (fa_spec_t *)calloc(1, sizeof(fa_spec_t));
+  if (!sp) return NULL;
+  rng_t r;
+  rng_seed(&r, seed_a ^ 0xFA5Aull, seed_b);
+  sp->total = total_bytes;
+  sp->n_chrom = n_chrom;
+  sp->seed_a = seed_a;
+  sp->seed_b = seed_b;
+  for (int f = 0; f < FA_NFAM; ++f) {
+    sp->flen[f] = (uint32_t)rng_loguniform(&r, 300.0, 6000.0);
+    sp->fam[f] = (uint8_t *)malloc(sp->flen[f]);
+    for (uint32_t i = 0; i < sp->flen[f]; ++i) sp->fam[f][i] = (uint8_t)BASES[rng_next(&r) >> 62];
+  }
   double u[FA_MAX_CHROM], su = 0;
-  for (int k = 0; k < n_chrom; ++k) { u[k] = 0.5e9 + 2.0e9 * rng_unit(&g->r); su += u[k]; }
+  for (int k = 0; k < n_chrom; ++k) { u[k] = 0.5e9 + 2.0e9 * rng_unit(&r); su += u[k]; }
   double hdr = 0;
   for (int k = 0; k < n_chrom; ++k) hdr += (k + 1 < 10) ? 6 : 7;
   double bases = ((double)total_bytes - hdr) * 60.0 / 61.0;
   if (bases < n_chrom) bases = n_chrom;
   double top = 2.5e9 * n_chrom, gap = top - su;
   double s = gap > 0 ? (top - bases) / gap : -1;
+  uint64_t off = 0;
   for (int k = 0; k < n_chrom; ++k) {
     double L = (s >= 0 && s <= 1) ? 2.5e9 - s * (2.5e9 - u[k]) : u[k] * (bases / su);
-    g->clen[k] = L < 1 ? 1 : (uint64_t)L;
+    sp->clen[k] = L < 1 ? 1 : (uint64_t)L;
+    sp->coff[k] = off;
+    uint64_t b = fa_record_bytes(k, sp->clen[k]);
+    if (k == n_chrom - 1 || off + b >= total_bytes) {
+      /* this record runs to the end of the file */
+      sp->cbytes[k] = total_bytes > off ? total_bytes - off : 0;
+      sp->clen[k] = UINT64_MAX / 4;
+      sp->n_chrom = k + 1;
+      break;
+    }
+    sp->cbytes[k] = b;
+    off += b;
   }
-  g->clen[n_chrom - 1] = UINT64_MAX / 4; /* the last chromosome runs to total_bytes */
-  g->chrom = 0;
-  fa_begin_chrom(g);
+  return sp;
+}
+
+static void fa_spec_free(fa_spec_t *sp) {
+  if (!sp) return;
+  for (int f = 0; f < FA_NFAM; ++f) free(sp->fam[f]);
+  free(sp);
+}
+
+typedef struct {
+  fa_spec_t *sp;
+  fa_chrom_t c;
+  int k;
+  uint64_t emitted;
+} fasta_t;
+
+void *synth_fasta_new(uint64_t seed_a, uint64_t seed_b, uint64_t total_bytes, int n_chrom) {
+  fasta_t *g = (fasta_t *)calloc(1, sizeof(fasta_t));
+  if (!g) return NULL;
+  g->sp = fa_spec_new(seed_a, seed_b, total_bytes, n_chrom);
+  if (!g->sp) { free(g); return NULL; }
+  g->k = 0;
+  fa_chrom_init(&g->c, g->sp, 0);
   return g;
 }
 
 void synth_fasta_free(void *p) {
   fasta_t *g = (fasta_t *)p;
   if (!g) return;
-  for (int f = 0; f < FA_NFAM; ++f) free(g->fam[f]);
+  fa_spec_free(g->sp);
   free(g);
 }
 
@@ -441,27 +512,59 @@ void synth_fasta_free(void *p) {
 uint64_t synth_fasta_read(void *p, uint8_t *out, uint64_t n) {
   fasta_t *g = (fasta_t *)p;
   uint64_t w = 0;
-  while (w < n && g->emitted < g->total) {
-    if (g->hdr_at < g->hdr_len) { out[w++] = (uint8_t)g->hdr[g->hdr_at++]; ++g->emitted; continue; }
-    if (g->need_newline_at_end) {
-      out[w++] = '\n'; ++g->emitted;
-      g->need_newline_at_end = 0;
-      ++g->chrom;
-      fa_begin_chrom(g);
-      continue;
-    }
-    if (g->col == 60) { out[w++] = '\n'; ++g->emitted; g->col = 0; continue; }
-    out[w++] = fa_base(g); ++g->emitted;
-    ++g->col; ++g->pos;
-    if (g->pos == g->clen[g->chrom]) {
-      if (g->col == 60) g->col = 0;
-      g->need_newline_at_end = 1;
+  while (w < n && g->k < g->sp->n_chrom) {
+    uint64_t got = fa_chrom_read(&g->c, out + w, n - w);
+    w += got;
+    g->emitted += got;
+    if (g->c.emitted >= g->c.limit) {
+      if (++g->k < g->sp->n_chrom) fa_chrom_init(&g->c, g->sp, g->k);
     }
   }
   return w;
 }
 
 uint64_t synth_fasta_emitted(void *p) { return ((fasta_t *)p)->emitted; }
+
+typedef struct {
+  const fa_spec_t *sp;
+  uint8_t *out;
+  int next;
+  pthread_mutex_t mu;
+} fa_fill_t;
+
+static void *fa_fill_worker(void *arg) {
+  fa_fill_t *F = (fa_fill_t *)arg;
+  for (;;) {
+    pthread_mutex_lock(&F->mu);
+    int k = F->next++;
+    pthread_mutex_unlock(&F->mu);
+    if (k >= F->sp->n_chrom) break;
+    fa_chrom_t c;
+    fa_chrom_init(&c, F->sp, k);
+    fa_chrom_read(&c, F->out + F->sp->coff[k], F->sp->cbytes[k]);
+  }
+  return NULL;
+}
+
+/* the whole file into out[0..total_bytes), chromosomes generated by up to
+ * `threads` threads (same bytes as the streaming reader) */
+int synth_fasta_fill(uint64_t seed_a, uint64_t seed_b, uint64_t total_bytes, int n_chrom, int threads, uint8_t *out) {
+  fa_spec_t *sp = fa_spec_new(seed_a, seed_b, total_bytes, n_chrom);
+  if (!sp) return -1;
+  fa_fill_t F;
+  F.sp = sp;
+  F.out = out;
+  F.next = 0;
+  pthread_mutex_init(&F.mu, NULL);
+  if (threads < 1) threads = 1;
+  if (threads > 64) threads = 64;
+  pthread_t th[64];
+  for (int t = 0; t < threads; ++t) pthread_create(&th[t], NULL, fa_fill_worker, &F);
+  for (int t = 0; t < threads; ++t) pthread_join(th[t], NULL);
+  pthread_mutex_destroy(&F.mu);
+  fa_spec_free(sp);
+  return 0;
+}
 
 /* ------------------------------------------------------------- misc draws */
 

@@ -266,3 +266,55 @@ def test_out_cap_checked():
         with pytest.raises(ace.AceapexError) as e:
             arc.decode_all(small)
         assert e.value.code == ace.ERANGE
+
+
+# ------------------------------------------------------- launch knobs / tuner
+
+def test_launch_knobs_same_output():
+    """Every launch shape gives the same bytes, including a staging size that
+    forces the global staging slot and a single working warp per CTA."""
+    d = synth.pe_fastq(6 << 20, ref_len=2_000_000)
+    a = ace.encode(d, min_match=12)
+    with ace.Archive(a) as arc:
+        lim = arc.get_launch()["max_ctas"]
+        for ctas, warps, stage in [(0, 0, 0), (1, 1, 0), (lim // 2, 7, 64), (3, 32, 1024), (lim, 16, 3072)]:
+            arc.set_launch(ctas, warps, stage)
+            got = arc.get_launch()
+            assert got["warps_per_cta"] == (warps or 32) and got["stage_bytes"] == (stage or 3072)
+            out = torch.zeros(arc.size, dtype=torch.uint8, device="cuda")
+            arc.decode_all(out)
+            arc.check()
+            assert_same(out.cpu().numpy(), d)
+        with pytest.raises(ace.AceapexError):
+            arc.set_launch(0, 33, 0)
+
+
+def test_batch_graph_replay_and_autotune(tmp_path):
+    from paper_2606_18900_gb300 import autotune
+    sizes = synth.batch_sizes(24, seed=13, hi=1 << 21)
+    datas = synth.batch_fastq(sizes, seed=13, ref_len=1_000_000)
+    arcs = [ace.Archive(ace.encode(x, min_match=16, threads=1)) for x in datas]
+    outs = [torch.zeros(x.size, dtype=torch.uint8, device="cuda") for x in datas]
+    s = torch.cuda.Stream()
+    run = lambda: ace.decode_batch(arcs, outs, s)
+    cands = [(8, 32, 3072), (arcs[0].get_launch()["max_ctas"], 16, 1024)]
+    cfg, table = autotune.tune(arcs[0], run, key="test", stream=s, reps=1, cands=cands,
+                               cache_path=str(tmp_path / "tune.json"))
+    assert len(table) == 2 and cfg in [dict(t[0], ms=t[1]) for t in table]
+    cfg2, table2 = autotune.tune(arcs[0], run, key="test", stream=s, cache_path=str(tmp_path / "tune.json"))
+    assert table2 == [] and cfg2 == cfg          # served from the cache
+    run()
+    arcs[0].check(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        run()
+    for _ in range(3):
+        for o in outs:
+            o.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert arcs[0].last_error() == ace.OK
+        for x, o in zip(datas, outs):
+            assert_same(o.cpu().numpy(), x)
+    for a in arcs:
+        a.close()

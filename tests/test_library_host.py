@@ -76,6 +76,19 @@ def test_library_encoder_params():
     assert np.array_equal(oracle.decode(a), f)
 
 
+@pytest.mark.parametrize("mm", [32, 48])
+def test_library_encoder_sampled_long_matches(mm):
+    """Long minimum matches switch the encoder to content-defined anchors with
+    backward extension; archives still decode exactly under the oracle and
+    respect every format rule (checked by the oracle's decoder)."""
+    f = synth.fasta(3_000_000, seed=7, n_chrom=3)
+    for D in (0, 1 << 20):
+        a = ace.encode(f, min_match=mm, dist_bound=D)
+        assert np.array_equal(oracle.decode(a), f)
+        assert ace.encode(f, min_match=mm, dist_bound=D, threads=1).tobytes() == a.tobytes()
+    assert a.size < f.size / 2
+
+
 def test_library_encoder_deterministic_across_threads():
     d = synth.pe_fastq(4 << 20, ref_len=2_000_000)
     a1 = ace.encode(d, threads=1, min_match=16)
