@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="fastq", choices=["fastq", "tiny", "batch", "genome"])
+    p.add_argument("--workload", default="fastq", choices=["fastq", "tiny", "batch", "genome", "serve"])
     p.add_argument("--log2-block", type=int, default=14)
     p.add_argument("--size", type=int, default=0, help="workload bytes (0 = the workload's default)")
     p.add_argument("--min-match", type=int, default=0, help="0 = the workload's default")
@@ -56,6 +56,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--rates", default="1000,10000,100000", help="serve: arrival rates per second")
+    p.add_argument("--requests", type=int, default=3000, help="serve: requests per rate")
+    p.add_argument("--budget", type=int, default=8 << 30, help="serve: device-memory budget")
+    p.add_argument("--slots", type=int, default=4, help="serve: batches in flight")
     return p.parse_args()
 
 
@@ -483,6 +487,95 @@ def workload_genome(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------- serve
+
+def workload_serve(args):
+    """Continuous-batching server over the tiny FASTQ and a genome (3 GB by
+    default), Poisson arrivals: 90% read lookups, 10% ranges log-uniform in
+    1 KiB-64 MiB. Against serial per-request decode of the same requests."""
+    import threading
+
+    import torch
+
+    import paper_2606_18900_gb300 as ace
+    import synth
+
+    fq = synth.tiny_fastq()
+    G = args.size or 3_000_000_000
+    t = time.perf_counter()
+    fa = synth.fasta(G, seed=5)
+    a_fq = ace.Archive(ace.encode(fq, min_match=16, reads=ace.fastq_index(fq)))
+    a_fa = ace.Archive(ace.encode(fa, min_match=32, dist_bound=1 << 30))
+    setup_s = time.perf_counter() - t
+    src = [fq, fa]
+    results = {}
+    for rate in [float(x) for x in args.rates.split(",")]:
+        n = args.requests
+        rng = np.random.default_rng(int(rate))
+        reqs = []
+        for _ in range(n):
+            if rng.random() < 0.9:
+                lo, hi = a_fq.read_lookup(int(rng.integers(0, 2000)))
+                reqs.append((0, lo, hi))
+            else:
+                L = int(np.exp(rng.uniform(np.log(1024), np.log(64 << 20))))
+                lo = int(rng.integers(0, G - L))
+                reqs.append((1, lo, lo + L))
+        gaps = synth.poisson_gaps_ns(5, int(rate), n, rate)
+        outs = [torch.empty(hi - lo, dtype=torch.uint8, device="cuda") for _, lo, hi in reqs]
+        total_bytes = sum(hi - lo for _, lo, hi in reqs)
+        with ace.Server([a_fq, a_fa], mem_budget=args.budget, slots=args.slots) as srv:
+            tickets = [None] * n
+            t0 = time.perf_counter()
+            due = t0
+            for i, ((a, lo, hi), o) in enumerate(zip(reqs, outs)):
+                due += gaps[i] * 1e-9
+                while time.perf_counter() < due:
+                    pass
+                try:
+                    tickets[i] = srv.submit(a, lo, hi, o)
+                except ace.AceapexError as e:
+                    if e.code != ace.EBUSY:
+                        raise
+            t_sub = time.perf_counter() - t0
+            lat = [srv.wait(tk) for tk in tickets if tk is not None]
+            wall = time.perf_counter() - t0
+            st = srv.stats()
+        served = [i for i in range(n) if tickets[i] is not None]
+        total_bytes = sum(reqs[i][2] - reqs[i][1] for i in served)
+        torch.cuda.synchronize()
+        ok = all(np.array_equal(outs[i].cpu().numpy(), src[reqs[i][0]][reqs[i][1]:reqs[i][2]])
+                 for i in served[:: max(1, len(served) // 200)])
+        results[str(int(rate))] = {"p50_ms": pctl(lat, 50), "p99_ms": pctl(lat, 99), "gbs": total_bytes / wall / 1e9,
+                                   "offered_rate": rate, "achieved_submit_rate": n / t_sub, "batches": st["batches"],
+                                   "max_batch": st["max_batch"], "max_inflight": st["max_inflight"],
+                                   "refused": st["refused"], "bytes": total_bytes, "bit_exact_sample": ok}
+    # serial per-request decode (one request at a time, synchronous)
+    stream = torch.cuda.Stream()
+    arcs = [a_fq, a_fa]
+    lat_s, nbytes = [], 0
+    t0 = time.perf_counter()
+    for (a, lo, hi), o in [(reqs[i], outs[i]) for i in served][:1000]:
+        t = time.perf_counter()
+        arcs[a].decode_range(lo, hi, o, stream)
+        stream.synchronize()
+        lat_s.append((time.perf_counter() - t) * 1e3)
+        nbytes += hi - lo
+    serial_s = time.perf_counter() - t0
+    for a in arcs:
+        a.check(stream)
+    best = max(results.values(), key=lambda r: r["gbs"])
+    line = base_line(args, best["gbs"], None, 1,
+                     {"workload": f"serving: tiny FASTQ + {G}-byte genome resident; Poisson arrivals, 90% read "
+                                  "lookups / 10% ranges log-uniform 1 KiB-64 MiB",
+                      "budget_bytes": args.budget, "slots": args.slots, "setup_seconds": round(setup_s, 1)},
+                     rates=results,
+                     serial_per_request={"p50_ms": pctl(lat_s, 50), "p99_ms": pctl(lat_s, 99),
+                                         "gbs": nbytes / serial_s / 1e9, "n": len(lat_s)},
+                     gpu_launches=None, bit_exact=all(r["bit_exact_sample"] for r in results.values()))
+    print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------------- reference
 
 def run_reference(args):
@@ -534,6 +627,8 @@ def main():
         workload_tiny(args)
     elif args.workload == "batch":
         workload_batch(args)
+    elif args.workload == "serve":
+        workload_serve(args)
     else:
         workload_genome(args)
 

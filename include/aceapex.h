@@ -167,6 +167,47 @@ int aceapex_stream_range(aceapex_archive *a, uint64_t byte_lo, uint64_t byte_hi,
 int aceapex_decode_batch(aceapex_archive *const *as, int n, void *const *d_outs, void *stream);
 
 /*
+ * Serving engine (continuous batching over device-resident archives; the
+ * paper's random access, §4 and §4.1, for many concurrent requests).
+ *
+ * aceapex_server_create: serve the n archives as[0..n) (same device; the
+ * server does not own them and they must outlive it; do not call other
+ * decode functions on them while the server runs). mem_budget: device bytes
+ * for the server (per-slot page tables and flags, 8 bytes per segment per
+ * slot, and the decode arenas, the rest split evenly over the slots). slots:
+ * batches that may be in flight at once (1..64), each on its own stream. A
+ * worker thread forms batches from the queue in arrival order while the union
+ * of the requests' source closures fits a slot's arena, and launches a batch
+ * whenever a slot is free, so requests that arrive while batches run are
+ * decoded in the next batch, overlapping with them.
+ *
+ * aceapex_server_submit: queue bytes [byte_lo, byte_hi) of archive `arc`, to
+ * be written to the device buffer d_dst (cap bytes, caller-owned, must stay
+ * valid until the request completes). Returns a ticket. EBUSY: the request's
+ * closure alone exceeds a slot's arena (admission refused); ERANGE, EINVAL.
+ *
+ * aceapex_server_poll: *done = 1 once the request completed (then the ticket
+ * is released, the return value is the request's status and *latency_ms the
+ * time from submission to completion); *done = 0 while pending (return
+ * ACEAPEX_OK). wait != 0 blocks until completion.
+ */
+typedef struct aceapex_server aceapex_server;
+typedef struct {
+  uint64_t submitted, completed, refused, batches, bytes_served;
+  uint64_t max_batch;      /* most requests in one batch */
+  uint64_t max_inflight;   /* most batches in flight at once */
+  uint64_t queued;         /* requests waiting now */
+  uint64_t slot_segments;  /* arena capacity of a slot, in segments */
+} aceapex_server_stats;
+
+int aceapex_server_create(aceapex_archive *const *as, int n, uint64_t mem_budget, int slots, aceapex_server **out);
+void aceapex_server_destroy(aceapex_server *s);
+int aceapex_server_submit(aceapex_server *s, int arc, uint64_t byte_lo, uint64_t byte_hi, void *d_dst, uint64_t cap,
+                          uint64_t *ticket);
+int aceapex_server_poll(aceapex_server *s, uint64_t ticket, int wait, int *done, double *latency_ms);
+int aceapex_server_get_stats(aceapex_server *s, aceapex_server_stats *out);
+
+/*
  * Allocation-free whole-file decode. The paper has no counterpart; this entry
  * point exists for callers that cannot allocate device memory when they
  * decode: for example a program that gives all device memory to its own pool

@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _SO = os.path.join(_HERE, "libaceapex.so")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
-_SOURCES = ["kernels.cu", "host.cpp", "encoder.cpp"]
+_SOURCES = ["kernels.cu", "host.cpp", "encoder.cpp", "server.cpp"]
 _lock = threading.Lock()
 _lib = None
 
@@ -48,7 +48,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile libaceapex.so in-tree for sm_103a (three translation units in
     parallel, then one link)."""
     srcs = [os.path.join(_CSRC, s) for s in _SOURCES]
-    deps = srcs + [os.path.join(_CSRC, h) for h in ("format.h", "kernels.h")] + [os.path.join(_INCLUDE, "aceapex.h")]
+    deps = srcs + [os.path.join(_CSRC, h) for h in ("format.h", "kernels.h", "archive.h")] + [os.path.join(_INCLUDE, "aceapex.h")]
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(os.path.getmtime(d) for d in deps):
         return _SO
     nvcc = _nvcc()
@@ -87,6 +87,14 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "completed", "refused", "batches", "bytes_served",
+                                               "max_batch", "max_inflight", "queued", "slot_segments")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def lib():
     """The loaded library (built first when out of date)."""
     global _lib
@@ -117,6 +125,16 @@ def lib():
             u32p = ctypes.POINTER(ctypes.c_uint32)
             L.aceapex_get_launch.argtypes = [vp, u32p, u32p, u32p, u32p]
             L.aceapex_get_launch.restype = i32
+            L.aceapex_server_create.argtypes = [ctypes.POINTER(vp), i32, u64, i32, ctypes.POINTER(vp)]
+            L.aceapex_server_create.restype = i32
+            L.aceapex_server_destroy.argtypes = [vp]
+            L.aceapex_server_destroy.restype = None
+            L.aceapex_server_submit.argtypes = [vp, i32, u64, u64, vp, u64, u64p]
+            L.aceapex_server_submit.restype = i32
+            L.aceapex_server_poll.argtypes = [vp, u64, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]
+            L.aceapex_server_poll.restype = i32
+            L.aceapex_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+            L.aceapex_server_get_stats.restype = i32
             L.aceapex_decode_all_noalloc.argtypes = [vp, u64, vp, u64, vp, vp]
             L.aceapex_decode_all_noalloc.restype = i32
             L.aceapex_free.argtypes = [vp]
@@ -280,6 +298,62 @@ class Archive:
         _check(lib().aceapex_debug_block_segments(
             self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)) if a.size else None, a.size),
             "aceapex_debug_block_segments")
+
+
+class Server:
+    """Continuous-batching serving engine over device-resident archives
+    (aceapex_server_*). Results land in caller-owned device buffers."""
+
+    def __init__(self, archives, mem_budget: int = 2 << 30, slots: int = 4):
+        self.archives = list(archives)          # keep the handles alive
+        hs = (ctypes.c_void_p * len(self.archives))(*[a.handle for a in self.archives])
+        h = ctypes.c_void_p()
+        _check(lib().aceapex_server_create(hs, len(self.archives), mem_budget, slots, ctypes.byref(h)),
+               "aceapex_server_create")
+        self._h = h
+
+    def submit(self, arc: int, lo: int, hi: int, out) -> int:
+        """Queue [lo, hi) of archive `arc` into device tensor `out`; returns a ticket."""
+        t = ctypes.c_uint64()
+        _check(lib().aceapex_server_submit(self._h, arc, lo, hi, _ptr(out), out.numel() * out.element_size(),
+                                           ctypes.byref(t)), "aceapex_server_submit")
+        return t.value
+
+    def poll(self, ticket: int, wait: bool = False):
+        """None while pending; else the latency in ms (raises on a failed request)."""
+        done = ctypes.c_int()
+        lat = ctypes.c_double()
+        rc = lib().aceapex_server_poll(self._h, ticket, int(wait), ctypes.byref(done), ctypes.byref(lat))
+        if not done.value:
+            _check(rc, "aceapex_server_poll")
+            return None
+        _check(rc, "served request")
+        return lat.value
+
+    def wait(self, ticket: int) -> float:
+        return self.poll(ticket, True)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().aceapex_server_get_stats(self._h, ctypes.byref(st)), "aceapex_server_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().aceapex_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def decode_all_noalloc(d_archive, nbytes: int, out, status, stream=None) -> int:

@@ -12,9 +12,7 @@
 #include <new>
 #include <vector>
 
-#include "aceapex.h"
-#include "format.h"
-#include "kernels.h"
+#include "archive.h"
 
 namespace aceapex {
 int encode_archive(const uint8_t *in, uint64_t n, uint32_t log2_B, uint32_t min_match, uint32_t cap, uint64_t D,
@@ -24,17 +22,7 @@ uint64_t fastq_index(const uint8_t *in, uint64_t n, uint64_t *out, uint64_t cap)
 
 using namespace aceapex;
 
-namespace {
-
-constexpr int kBlock = (int)kDecodeThreads;
-constexpr uint64_t kDefaultWaitNs = 2000000000ull;
-
-template <class T>
-T rd(const uint8_t *p) {
-  T v;
-  std::memcpy(&v, p, sizeof(T));
-  return v;
-}
+namespace aceapex {
 
 // One library-wide epoch counter per device: epochs never repeat on a device,
 // so a ready flag can never be mistaken for one of another call.
@@ -54,134 +42,10 @@ uint32_t *global_epoch(int device) {
   return d.d_global_epoch;
 }
 
-// device buffer that owns its memory
-template <class T>
-struct DBuf {
-  T *p = nullptr;
-  uint64_t n = 0;
-  cudaError_t alloc(uint64_t count) {
-    release();
-    n = count;
-    if (!count) return cudaSuccess;
-    return cudaMalloc(&p, count * sizeof(T));
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    n = 0;
-  }
-};
+}  // namespace aceapex
 
-// pinned host staging whose previous async copy is waited for before reuse
-struct Staging {
-  void *p = nullptr;
-  uint64_t bytes = 0;
-  cudaEvent_t done = nullptr;
-  bool pending = false;
-  cudaError_t reserve(uint64_t b) {
-    if (pending) cudaEventSynchronize(done), pending = false;
-    if (b <= bytes) return cudaSuccess;
-    if (p) cudaFreeHost(p);
-    p = nullptr;
-    bytes = 0;
-    cudaError_t e = cudaMallocHost(&p, b);
-    if (e == cudaSuccess) bytes = b;
-    if (!done) cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
-    return e;
-  }
-  void mark(cudaStream_t st) {
-    cudaEventRecord(done, st);
-    pending = true;
-  }
-  void release() {
-    if (pending) cudaEventSynchronize(done);
-    if (p) cudaFreeHost(p);
-    if (done) cudaEventDestroy(done);
-    p = nullptr;
-    done = nullptr;
-    bytes = 0;
-    pending = false;
-  }
-};
 
-int cuda_status(cudaError_t e) { return e == cudaSuccess ? ACEAPEX_OK : ACEAPEX_ECUDA; }
-
-}  // namespace
-
-struct aceapex_archive {
-  int device = 0;
-  Header h{};
-  std::vector<SegRec> dir;
-  std::vector<uint64_t> dep_ptr;
-  std::vector<uint32_t> deps;
-  std::vector<uint64_t> reads;
-  aceapex_stats stats{};
-
-  DBuf<uint8_t> d_payload;
-  DBuf<SegRec> d_dir;
-  DBuf<uint32_t> d_lut;
-  DBuf<uint32_t> d_flags;
-  DBuf<WorkItem> d_order;    // all segments in level order
-  DBuf<uint32_t> d_words;    // [0] err, [1] epoch, [2] counter
-  DBuf<uint8_t> d_blocked;
-  DBuf<uint8_t> d_scratch;
-  uint32_t scratch_warps = 0;
-  int grid = 0;       // CTAs of the current launch configuration
-  int max_grid = 0;   // occupancy limit (scratch is sized for it)
-  uint32_t active_warps = kDecodeThreads / 32;
-  uint32_t stage_cap = kSmemStage;
-  uint32_t max_cmd_syms = 0;  // largest n_cmd * (4 + W) of any segment
-  uint64_t wait_ns = kDefaultWaitNs;
-  bool any_blocked = false;
-
-  // range decode: page table, arena of slots, work list
-  DBuf<uint32_t> d_page;
-  DBuf<uint8_t> d_arena;
-  DBuf<WorkItem> d_work;
-  Staging stage_work;
-  std::vector<uint32_t> mark;
-  uint32_t mark_gen = 0;
-
-  // ring streaming
-  DBuf<uint8_t> d_ring;
-  DBuf<uint32_t> d_seg_crc;
-  // batch
-  std::vector<uint8_t> batch_desc;  // host copy of what d_batch_arcs / d_batch_views hold
-  DBuf<DevArchive> d_batch_arcs;
-  DBuf<OutView> d_batch_views;
-  Staging stage_batch;
-
-  uint32_t *err() const { return d_words.p; }
-  uint32_t *epoch() const { return d_words.p + 1; }
-  uint32_t *counter() const { return d_words.p + 2; }
-
-  DevArchive dev() const {
-    DevArchive A{};
-    A.payload = d_payload.p;
-    A.dir = d_dir.p;
-    A.order = d_order.p;
-    A.lut = d_lut.p;
-    A.flags = d_flags.p;
-    A.blocked = any_blocked ? d_blocked.p : nullptr;
-    A.n = h.n;
-    A.D = h.D;
-    A.log2_S = h.log2_S;
-    A.W = h.W;
-    A.min_match = h.min_match;
-    A.n_seg = (uint32_t)h.n_seg;
-    return A;
-  }
-
-  void release() {
-    d_payload.release(); d_dir.release(); d_lut.release(); d_flags.release(); d_order.release();
-    d_words.release(); d_blocked.release(); d_scratch.release(); d_page.release(); d_arena.release();
-    d_work.release(); d_ring.release(); d_seg_crc.release(); d_batch_arcs.release(); d_batch_views.release();
-    stage_work.release();
-    stage_batch.release();
-  }
-};
-
-namespace {
+namespace aceapex {
 
 // FORMAT.md §6 host-side checks; fills h, dir, dep_ptr, deps, reads, stats.
 int validate(const uint8_t *a, uint64_t len, aceapex_archive *A) {
@@ -380,6 +244,34 @@ void closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, std::vector<uint3
   }
 }
 
+void closure_of(aceapex_archive *A, const uint32_t *seeds, uint64_t n, std::vector<uint32_t> &out) {
+  if (A->mark.size() != A->h.n_seg) A->mark.assign(A->h.n_seg, 0);
+  if (++A->mark_gen == 0) {
+    std::fill(A->mark.begin(), A->mark.end(), 0);
+    A->mark_gen = 1;
+  }
+  const uint32_t g = A->mark_gen;
+  out.clear();
+  std::vector<uint32_t> stack;
+  for (uint64_t i = 0; i < n; ++i)
+    if (A->mark[seeds[i]] != g) {
+      A->mark[seeds[i]] = g;
+      stack.push_back(seeds[i]);
+    }
+  while (!stack.empty()) {
+    uint32_t s = stack.back();
+    stack.pop_back();
+    out.push_back(s);
+    for (uint64_t i = A->dep_ptr[s]; i < A->dep_ptr[s + 1]; ++i) {
+      uint32_t d = A->deps[i];
+      if (A->mark[d] != g) {
+        A->mark[d] = g;
+        stack.push_back(d);
+      }
+    }
+  }
+}
+
 // decode the closure of [s_lo, s_hi] into arena slots (paged view); returns the view
 int decode_closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, cudaStream_t st, OutView *view_out,
                    uint32_t *n_out, bool begin) {
@@ -425,7 +317,7 @@ int decode_closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, cudaStream_
   return ACEAPEX_OK;
 }
 
-}  // namespace
+}  // namespace aceapex
 
 // ====================================================================== C ABI
 

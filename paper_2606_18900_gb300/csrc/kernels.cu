@@ -513,6 +513,26 @@ __global__ void gather_kernel(OutView v, uint32_t log2_S, uint64_t lo, uint64_t 
   }
 }
 
+constexpr uint64_t kGatherChunk = 65536;
+
+__global__ void multi_gather_kernel(const GatherJob *jobs, uint32_t n_jobs, uint64_t n_chunks) {
+  for (uint64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+    // the job holding chunk c: largest j with jobs[j].chunk0 <= c
+    uint32_t lo = 0, hi = n_jobs;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (jobs[mid].chunk0 <= c) lo = mid;
+      else hi = mid;
+    }
+    const GatherJob &J = jobs[lo];
+    const uint64_t a = (c - J.chunk0) * kGatherChunk, b = min(J.n, a + kGatherChunk);
+    for (uint64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+      const uint8_t *p = at(J.v, J.lo + i, J.log2_S);
+      J.dst[i] = p ? *p : 0;
+    }
+  }
+}
+
 __global__ void set_pages_kernel(uint32_t *page, const WorkItem *work, uint32_t n) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) page[work[i].seg] = i;
@@ -667,6 +687,13 @@ cudaError_t launch_gather(OutView v, uint32_t log2_S, uint64_t lo, uint64_t hi, 
   uint64_t n = hi - lo;
   int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   gather_kernel<<<grid, 256, 0, st>>>(v, log2_S, lo, n, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi_gather(const GatherJob *jobs, uint32_t n_jobs, uint64_t n_chunks, cudaStream_t st) {
+  if (!n_jobs || !n_chunks) return cudaSuccess;
+  const int grid = (int)(n_chunks < 4096 ? n_chunks : 4096);
+  multi_gather_kernel<<<grid, 256, 0, st>>>(jobs, n_jobs, n_chunks);
   return cudaGetLastError();
 }
 

@@ -97,6 +97,18 @@ cudaError_t launch_gather(OutView v, uint32_t log2_S, uint64_t lo, uint64_t hi, 
 // page[work[i].seg] = i for i < n (paged views)
 cudaError_t launch_set_pages(uint32_t *page, const WorkItem *work, uint32_t n, cudaStream_t st);
 
+// One request of a served batch: copy [lo, lo + n) of view v to dst.
+struct GatherJob {
+  OutView v;
+  uint64_t lo, n;
+  uint8_t *dst;
+  uint64_t chunk0;  // first 64 KiB chunk of this job in the launch
+  uint32_t log2_S, pad;
+};
+
+// All jobs in one launch: the jobs' 64 KiB chunks are spread over the CTAs.
+cudaError_t launch_multi_gather(const GatherJob *jobs, uint32_t n_jobs, uint64_t n_chunks, cudaStream_t st);
+
 // CRC-32 of each window [lo + k*window, ...) of the ring view, written to crc[k].
 cudaError_t launch_window_crc(OutView v, uint64_t lo, uint64_t hi, uint64_t window, uint32_t *crc, uint32_t *seg_crc,
                               uint32_t log2_S, cudaStream_t st);
