@@ -175,25 +175,47 @@ def cpu_oracle_baseline(arc, data, what):
 
 # ------------------------------------------------------------------- fastq
 
+def shared_archive(make, path, rank, world):
+    """Rank 0 runs make() (the encoder) once and publishes the archive at
+    `path`; the other ranks wait at a barrier and read it. Returns (archive,
+    seconds rank 0 spent in make)."""
+    if world > 1 and rank != 0:
+        import torch.distributed as dist
+        dist.barrier()
+        return np.fromfile(path, dtype=np.uint8), 0.0
+    t = time.perf_counter()
+    arc = make()
+    dt = time.perf_counter() - t
+    if world > 1:
+        import torch.distributed as dist
+        arc.tofile(path + ".tmp")
+        os.replace(path + ".tmp", path)
+        dist.barrier()
+    return arc, dt
+
+
+def max_over_ranks(value, world, device="cpu"):
+    """The slowest rank's time: all-reduce MAX (identity for one rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_fastq(size, log2_block, min_match, rank, world):
-    """The paired-end FASTQ workload encoded by the library encoder. With several
-    ranks, rank 0 encodes once and shares the archive via /dev/shm."""
+    """The paired-end FASTQ workload encoded by the library encoder; with
+    several ranks, one replica shared through /dev/shm."""
     import paper_2606_18900_gb300 as ace
     import synth
 
     data = synth.pe_fastq(size)
     path = f"/dev/shm/aceapex_bench_{size}_{log2_block}_{min_match}.bin"
-    if world > 1 and rank != 0:
-        import torch.distributed as dist
-        dist.barrier()
-        return data, np.fromfile(path, dtype=np.uint8), 0.0
-    t = time.perf_counter()
-    arc = ace.encode(data, log2_B=log2_block, min_match=min_match, reads=ace.fastq_index(data))
-    enc_s = time.perf_counter() - t
-    if world > 1:
-        import torch.distributed as dist
-        arc.tofile(path)
-        dist.barrier()
+    arc, enc_s = shared_archive(
+        lambda: ace.encode(data, log2_B=log2_block, min_match=min_match, reads=ace.fastq_index(data)), path, rank,
+        world)
     return data, arc, enc_s
 
 
@@ -262,11 +284,7 @@ def workload_fastq(args):
     sustain(run, 0.4)
     clk = clocks.stop()
     arc.check(stream)
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(step_ms)), world, f"cuda:{local}")
     value = N * world * args.steps / (total_ms * 1e-3) / 1e9
     avg_ms = float(np.mean(step_ms))
     peak, peak_kind = read_peaks()
