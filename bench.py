@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="fastq", choices=["fastq", "tiny", "batch", "genome", "serve"])
+    p.add_argument("--workload", default="fastq", choices=["fastq", "tiny", "batch", "genome", "serve", "entropy"])
     p.add_argument("--log2-block", type=int, default=14)
     p.add_argument("--size", type=int, default=0, help="workload bytes (0 = the workload's default)")
     p.add_argument("--min-match", type=int, default=0, help="0 = the workload's default")
@@ -374,6 +374,74 @@ def workload_tiny(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------- entropy
+
+# Warp instructions one literal step needs at least (32 symbols): slot mask,
+# table address, table load, frequency and bias extraction (4), state shift,
+# multiply-add, renormalisation compare, ballot, lane-mask and popc for the
+# word index, ring index mask and address, ring load, word insertion (2),
+# popc and add for the word pointer, cursor compare and branch, output
+# address (2), byte store.
+RANS_STEP_OPS = 27
+
+
+def workload_entropy(args):
+    """The entropy stage alone: a literal-only archive (no matches) of
+    back-to-back FASTQ quality strings, 4,096 streams of 64 KiB by default, each
+    16 KiB segment one 32-lane interleaved rANS message of 16,384 symbols."""
+    import torch
+
+    import paper_2606_18900_gb300 as ace
+    import synth
+
+    size = args.size or 4096 * 65536
+    data = synth.qualities(size)
+    t = time.perf_counter()
+    arc_bytes = ace.encode(data, log2_B=args.log2_block, min_match=255)
+    enc_s = time.perf_counter() - t
+    arc = ace.Archive(arc_bytes)
+    st = arc.stats()
+    if st["match_bytes"] != 0:
+        raise SystemExit("bench: the entropy workload must have no matches")
+    out = torch.empty(size, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    run = lambda: arc.decode_all(out, stream)
+    for _ in range(args.warmup):
+        run()
+    arc.check(stream)
+    ok = bool(np.array_equal(out.cpu().numpy(), data))
+    if not ok:
+        raise SystemExit("bench: GPU output differs from the input")
+    clocks = Clocks(0)
+    clocks.start()
+    sustain(run, 0.4)
+    step_ms = timed_steps(run, stream, args.steps)
+    sustain(run, 0.4)
+    clk = clocks.stop()
+    arc.check(stream)
+    total_ms = float(sum(step_ms))
+    avg_s = total_ms / args.steps * 1e-3
+    sym_s = size / avg_s
+    props = torch.cuda.get_device_properties(0)
+    mhz = clk["sm_max_mhz"] if clk and clk.get("sm_max_mhz") else 2070.0
+    peak_sym = props.multi_processor_count * 4 * mhz * 1e6 / RANS_STEP_OPS * 32
+    C, U = st["compressed_bytes"], st["decoded_bytes"]
+    peak_hbm, kind = read_peaks()
+    config = {"workload": f"entropy stage alone: {size // 65536} x 64 KiB literal-only streams of FASTQ quality "
+                          f"symbols ({1 << args.log2_block}-byte segments, no matches)",
+              "bits_per_symbol": round(8 * C / U, 3), "C_bytes": C, "U_bytes": U, "encode_seconds": round(enc_s, 2),
+              "l2": "inputs larger than L2"}
+    line = base_line(args, size * args.steps / (total_ms * 1e-3) / 1e9, total_ms / args.steps, 1, config,
+                     symbols_per_s=sym_s,
+                     roofline={"bound": "alu", "achieved": sym_s / 1e9, "peak": peak_sym / 1e9, "unit": "Gsymbols/s",
+                               "frac": sym_s / peak_sym, "peak_kind": f"issue-limited model: {RANS_STEP_OPS} warp "
+                               f"instructions per 32 symbols, {props.multi_processor_count} SMs x 4 schedulers x "
+                               f"{mhz:.0f} MHz", "traffic": None, "kernel": "decode_kernel"},
+                     hbm_frac=(C + U) / avg_s / 1e9 / peak_hbm, gpu_launches=2 * args.steps, clocks=clk,
+                     bit_exact=ok)
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------- batch
 
 def workload_batch(args):
@@ -647,6 +715,8 @@ def main():
         workload_batch(args)
     elif args.workload == "serve":
         workload_serve(args)
+    elif args.workload == "entropy":
+        workload_entropy(args)
     else:
         workload_genome(args)
 

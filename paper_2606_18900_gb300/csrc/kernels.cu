@@ -4,19 +4,20 @@
 // §3.3 full pipeline; §4 range decode; §5 chunked range decode). Each warp
 // repeatedly takes the next work item from a global counter; the list is in
 // level order, so every segment a warp waits for was taken earlier by a warp
-// that is running (no deadlock, FORMAT.md §2 levels). Per segment:
-//   1. entropy phase: the 32 lanes run the 32 interleaved rANS states of the
-//      segment (FORMAT.md §4); the step's renormalisation words are handed out
-//      in ascending lane order with a ballot + popc, from a 64-word register
-//      window that is refilled 32 words at a time; symbols go to the warp's
-//      staging buffer. No dependency is needed for this phase.
-//   2. command phase: 32 commands at a time (one per lane) are parsed from the
-//      staged streams, positions come from warp scans, every rule of FORMAT.md
-//      §2 is checked, and each match's source segments are checked (level
-//      below ours, present in the view) and waited for (bounded wait on their
-//      ready flags). Then the warp copies the literal run and the match of
-//      each command in order, so intra-segment chains see earlier output.
-//   3. publish: every lane fences, then lane 0 stores the epoch into the
+// that is running (no deadlock, FORMAT.md §2 levels). Per segment (details at
+// decode_segment):
+//   1. rANS over the three command classes (FORMAT.md §4): the 32 lanes run
+//      the 32 interleaved states; each step's renormalisation words are handed
+//      out in ascending lane order with a ballot + popc, from a shared-memory
+//      ring that cp.async keeps filled ahead of the reader.
+//   2. command parse: 32 commands at a time, positions from warp scans, every
+//      rule of FORMAT.md §2 checked, source segments checked (level below
+//      ours, present in the view).
+//   3. rANS over the literal class, each literal stored straight to its
+//      output position.
+//   4. bounded waits on the ready flags of source segments, then match copies
+//      in hazard-free rounds spread over the lanes.
+//   5. publish: every lane fences, then lane 0 stores the epoch into the
 //      segment's flag with release semantics.
 // Errors latch the first code into a device word; waits give up at a time
 // limit (globaltimer) or as soon as another warp has latched an error.
@@ -25,6 +26,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "kernels.h"
 
@@ -120,6 +122,29 @@ __device__ __forceinline__ void st16(uint8_t *p, uint32_t v) { *reinterpret_cast
 
 constexpr int kViewLinear = 0, kViewRing = 1, kViewPaged = 2;
 
+// address of source position p in view v (its page is known to be present)
+template <int kMode>
+__device__ __forceinline__ const uint8_t *src_at(const OutView &v, uint64_t p, uint32_t log2_S) {
+  if (kMode == kViewPaged) return at(v, p, log2_S);
+  if (kMode == kViewRing) return v.base + ((p - v.origin) & v.mask);
+  return v.base + (p - v.origin);
+}
+
+// r = bytes c .. c+15 of the 32 bytes X || Y (bytes past the end read as 0)
+__device__ __forceinline__ void realign16(uint4 X, uint4 Y, uint32_t c, uint32_t r[4]) {
+  const uint32_t w[12] = {X.x, X.y, X.z, X.w, Y.x, Y.y, Y.z, Y.w, 0u, 0u, 0u, 0u};
+  const uint32_t k = c >> 2, sh = 8 * (c & 3);
+  uint32_t s4[8], s2[6], s1[5];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s4[j] = (k & 4) ? w[j + 4] : w[j];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) s2[j] = (k & 2) ? s4[j + 2] : s4[j];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) s1[j] = (k & 1) ? s2[j + 1] : s2[j];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) r[j] = __funnelshift_r(s1[j], s1[j + 1], sh);
+}
+
 // Per-warp shared table of the matches copied in one round.
 struct MatchTable {
   uint64_t src[32];
@@ -161,12 +186,17 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
   // the segment's own output is contiguous in every view
   uint8_t *const out = at(V, seg_start, log2_S);
   bool ok = out != nullptr;
+  // aligned 16-byte blocks of the view never straddle a segment (hence no ring
+  // wrap or page boundary either)
+  const bool vec =
+      log2_S >= 4 && (kMode == kViewPaged  ? (reinterpret_cast<uintptr_t>(V.slot_base) & 15) == 0
+                      : kMode == kViewRing ? ((reinterpret_cast<uintptr_t>(V.base) | V.origin) & 15) == 0
+                                           : ((reinterpret_cast<uintptr_t>(V.base) - V.origin) & 15) == 0);
 
   // ---------------------------------------------------------------- rANS
   const uint8_t *pl = A.payload + d.payload_off;
   uint32_t x = __ldg(reinterpret_cast<const uint32_t *>(pl) + lane);
   if (!__all_sync(kFull, x >= kRansL)) ok = false;
-  const uint16_t *words = reinterpret_cast<const uint16_t *>(pl + 128);
   // Renormalisation words go through a 512-word ring in shared memory, filled
   // by cp.async in blocks of 128 words two blocks ahead of the reader, so the
   // decode never waits on a global load between block boundaries. A lane
@@ -285,17 +315,29 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
       out[k + sh] = (uint8_t)sym;
     };
     if ((b3 & 31) && t0 - 32 + lane >= b3 && t0 - 32 + lane < n_sym) place(t0 - 32 + lane - b3, pend);
-    // full steps: every lane decodes, the class is known
+    // full steps: every lane decodes, the class is known. Four steps take at
+    // most 128 words, so after an advance() (blocks blk and blk + 1 complete,
+    // wp inside blk) four steps read only those two blocks, and the ring
+    // advances once per four steps.
     const uint32_t *lut3 = lut + (3u << kScaleBits);
-    for (; t0 + 32 <= n_sym; t0 += 32) {
+    auto lit_step = [&](uint32_t k) {
       const uint32_t e = lut3[x & (kScale - 1)];
       x = ((e >> 20) + 1u) * (x >> kScaleBits) + ((e >> 8) & 0xFFFu);
       const bool need = x < kRansL;
       const uint32_t m = __ballot_sync(kFull, need);
       if (need) x = (x << 16) | ring[(wp + __popc(m & lt)) & 511];
       wp += __popc(m);
+      place(k, e);
+    };
+    for (; t0 + 128 <= n_sym; t0 += 128) {
+      const uint32_t k = t0 + lane - b3;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) lit_step(k + 32 * u);
       advance();
-      place(t0 + lane - b3, e);
+    }
+    for (; t0 + 32 <= n_sym; t0 += 32) {
+      lit_step(t0 + lane - b3);
+      advance();
     }
     if (t0 < n_sym) {
       const uint32_t q = t0 + lane;
@@ -362,11 +404,15 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
         }
       }
       const bool ready = pending && !haz;
-      // units of 16 bytes: lane j copies units j, j+32, ... of the round, each
-      // with all of its loads in flight before its stores. Sources are read
-      // through L1: a 16 KiB segment never shares a sector or a line with
-      // another, and a segment is only read after its flag was acquired.
-      const uint32_t nu = ready ? (ml + 15) >> 4 : 0;
+      // Units: with vec, the 16-byte-aligned blocks of each match's output
+      // (a block's source bytes span at most two aligned source blocks, read
+      // with two 16-byte loads and realigned in registers; a whole block is
+      // stored with one 16-byte store, a partial one byte by byte); otherwise
+      // 16-byte pieces copied byte by byte. Lane j copies units j, j+32, ...
+      // of the round. Sources are read through L1: with vec an aligned source
+      // block never leaves its segment, and a segment is only read after its
+      // flag was acquired.
+      const uint32_t nu = !ready ? 0 : vec ? (((uint32_t)(dst - seg_start) & 15u) + ml + 15) >> 4 : (ml + 15) >> 4;
       const uint32_t incl = warp_incl_scan(nu, lane);
       const uint32_t total = __shfl_sync(kFull, incl, 31);
       mt->start[lane] = incl - nu;
@@ -378,24 +424,47 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
 #pragma unroll
         for (int st = 16; st; st >>= 1)
           if (mt->start[m + st] <= uu) m += st;
-        const uint32_t o = (uu - mt->start[m]) << 4;
-        const uint32_t n = min(16u, mt->len[m] - o);
-        const uint64_t p = mt->src[m] + o;
-        uint8_t *to = out + (mt->dst[m] - seg_start) + o;
-        uint8_t v[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          if ((uint32_t)j < n) {
-            const uint8_t *from;
-            if (kMode == kViewPaged) from = at(V, p + j, log2_S);
-            else if (kMode == kViewRing) from = V.base + ((p + j - V.origin) & V.mask);
-            else from = V.base + (p - V.origin) + j;
-            v[j] = *from;
+        if (vec) {
+          const uint32_t doff = (uint32_t)(mt->dst[m] - seg_start);
+          const uint32_t b16 = (doff & ~15u) + ((uu - mt->start[m]) << 4);
+          const uint32_t a0 = max(doff, b16), a1 = min(doff + mt->len[m], b16 + 16);
+          const uint32_t o = a0 - b16, n = a1 - a0;
+          const uint64_t P = mt->src[m] + (a0 - doff);
+          const uint8_t *pa = src_at<kMode>(V, P, log2_S);
+          const uint32_t dl = (uint32_t)reinterpret_cast<uintptr_t>(pa) & 15u;
+          uint4 X = make_uint4(0, 0, 0, 0), Y = X;
+          uint32_t c;
+          if (dl >= o) {
+            X = *reinterpret_cast<const uint4 *>(pa - dl);
+            if (dl + n > 16) Y = *reinterpret_cast<const uint4 *>(src_at<kMode>(V, P + (16 - dl), log2_S));
+            c = dl - o;
+          } else {
+            Y = *reinterpret_cast<const uint4 *>(pa - dl);
+            c = 16 + dl - o;
           }
-        }
+          uint32_t r[4];
+          realign16(X, Y, c, r);
+          uint8_t *to = out + b16;
+          if (n == 16) {
+            *reinterpret_cast<uint4 *>(to) = make_uint4(r[0], r[1], r[2], r[3]);
+          } else {
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if ((uint32_t)j < n) to[j] = v[j];
+            for (uint32_t i = 0; i < 16; ++i)
+              if (i - o < n) to[i] = (uint8_t)(r[i >> 2] >> (8 * (i & 3)));
+          }
+        } else {
+          const uint32_t o = (uu - mt->start[m]) << 4;
+          const uint32_t n = min(16u, mt->len[m] - o);
+          const uint64_t p = mt->src[m] + o;
+          uint8_t *to = out + (mt->dst[m] - seg_start) + o;
+          uint8_t v[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if ((uint32_t)j < n) v[j] = *src_at<kMode>(V, p + j, log2_S);
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if ((uint32_t)j < n) to[j] = v[j];
+        }
       }
       __syncwarp();
       pending = pending && !ready;
@@ -541,32 +610,57 @@ __global__ void set_pages_kernel(uint32_t *page, const WorkItem *work, uint32_t 
 // ------------------------------------------------------------------- CRC-32
 // Standard CRC-32 (reflected polynomial 0xEDB88320, init and xorout ~0).
 // A register r advanced over a message M from r0 is shift(r0, |M|) ^ raw(M),
-// where raw is the register from r0 = 0 and shift(r, L) multiplies by x^(8L)
-// mod P. So crc(A||B) = shift(crc(A), |B|) ^ crc(B), and crc(M) =
-// raw(M) ^ shift(~0, |M|) ^ ~0. shift() applies 32x32 GF(2) matrices for
-// L = 2^k bytes, built on the host by repeated squaring.
-__constant__ uint32_t c_crc_table[256];
-__constant__ uint32_t c_shift_op[48][32];  // op[k]: multiply by x^(8 * 2^k)
+// where raw is the register from r0 = 0 and shift(r, n) multiplies r by
+// x^(8n) mod P (n zero bytes). So raw(A||B) = shift(raw(A), |B|) ^ raw(B),
+// and crc(M) = raw(M) ^ shift(~0, |M|) ^ ~0. Everything is GF(2)-linear in
+// the bytes, which the kernels below use to hash pieces in any order.
+//
+// Table words (g_crc_tabs, filled once per device from the host):
+//   [0, 4096)                slice tables T_k[b] = raw(b followed by k zero
+//                            bytes), k = 0..15 (T_0 is the usual byte table)
+//   4096 + 1024 k + 256 i    byte tables of shift by 2^k bytes, k = 0..47:
+//                            entry v = shift(v << 8i, 2^k)
+constexpr int kCrcOps = 48;
+constexpr int kCrcTabWords = 4096 + kCrcOps * 1024;
+constexpr int kCrcSmemOps = 10;  // shifts by 2^0 .. 2^9 bytes kept in shared memory
+constexpr int kCrcSmemWords = 4096 + kCrcSmemOps * 1024;
+constexpr int kCrcThreads = 512;
+__device__ uint32_t g_crc_tabs[kCrcTabWords];
 
-__device__ __forceinline__ uint32_t gf2_apply(const uint32_t *op, uint32_t v) {
+__device__ __forceinline__ uint32_t crc_op(const uint32_t *t, uint32_t r) {
+  return t[r & 0xFFu] ^ t[256 + ((r >> 8) & 0xFFu)] ^ t[512 + ((r >> 16) & 0xFFu)] ^ t[768 + (r >> 24)];
+}
+
+// shift(r, n) with the byte tables of 2^k bytes at ops + 1024 k
+__device__ __forceinline__ uint32_t crc_shift(const uint32_t *ops, uint32_t r, uint64_t n) {
+  for (int k = 0; n; ++k, n >>= 1)
+    if (n & 1) r = crc_op(ops + 1024 * k, r);
+  return r;
+}
+
+// raw CRC of 16 bytes held little-endian in w
+__device__ __forceinline__ uint32_t crc_raw16(const uint32_t *T, uint4 w) {
+  const uint32_t v[4] = {w.x, w.y, w.z, w.w};
   uint32_t r = 0;
-#pragma unroll 8
-  for (int i = 0; i < 32; ++i)
-    if (v >> i & 1u) r ^= op[i];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) r ^= T[256 * (15 - m) + ((v[m >> 2] >> (8 * (m & 3))) & 0xFFu)];
   return r;
 }
 
-__device__ uint32_t crc_shift(uint32_t r, uint64_t len) {
-  for (int k = 0; len; ++k, len >>= 1)
-    if (len & 1) r = gf2_apply(c_shift_op[k], r);
-  return r;
-}
-
-// standard CRC of each segment piece [max(lo, seg), min(hi, seg_end)) of the view
-__global__ void seg_crc_kernel(OutView v, uint32_t log2_S, uint64_t lo, uint64_t hi, uint32_t *seg_crc) {
-  __shared__ uint32_t tab[256];
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) tab[i] = c_crc_table[i];
+// Raw CRC of each segment piece [max(lo, seg), min(hi, seg_end)) of the ring
+// view. One warp per piece,
+// persistent grid. The piece is read in rows of 512 bytes, lane j taking the
+// 16 bytes at 512 i + 16 j of row i (coalesced), and folds its 16-byte pieces
+// Horner-style with a shift of 512 bytes between rows; bytes after the last
+// full row are folded per lane. Each lane then shifts its register past the
+// bytes that follow its own last piece, and the warp XORs the 32 registers.
+__global__ void __launch_bounds__(kCrcThreads, 3) seg_crc_kernel(OutView v, uint32_t log2_S, uint64_t lo, uint64_t hi,
+                                                                  uint32_t *seg_crc) {
+  __shared__ uint32_t tab[kCrcSmemWords];
+  for (int i = threadIdx.x; i < kCrcSmemWords; i += blockDim.x) tab[i] = g_crc_tabs[i];
   __syncthreads();
+  const uint32_t *ops = tab + 4096;
+  const uint32_t *op512 = ops + 1024 * 9;
   const int lane = threadIdx.x & 31;
   const uint64_t S = uint64_t(1) << log2_S;
   const uint64_t first = lo >> log2_S, last = (hi - 1) >> log2_S;
@@ -576,25 +670,47 @@ __global__ void seg_crc_kernel(OutView v, uint32_t log2_S, uint64_t lo, uint64_t
     const uint64_t s = first + i;
     const uint64_t a = (s << log2_S) > lo ? (s << log2_S) : lo;
     const uint64_t b = ((s << log2_S) + S) < hi ? ((s << log2_S) + S) : hi;
-    const uint64_t len = b - a, chunk = (len + 31) / 32;
-    const uint64_t ca = a + lane * chunk, cb = ca + chunk < b ? ca + chunk : b;
-    uint32_t r = 0;
-    const uint8_t *p = ca < b ? at(v, ca, log2_S) : nullptr;
-    for (uint64_t k = 0; ca + k < cb; ++k) r = (r >> 8) ^ tab[(r ^ __ldcg(p + k)) & 0xFFu];
-    // fold lanes: raw(A||B) = shift(raw(A), |B|) ^ raw(B); shift each lane's
-    // register past the bytes that follow its chunk, then XOR all lanes
-    r = crc_shift(r, ca < b ? b - cb : 0);
+    const uint32_t len = (uint32_t)(b - a);
+    const uint8_t *p = v.base + ((a - v.origin) & v.mask);
+    // a piece with a full row has S >= 512 and starts at a multiple of S in a
+    // ring of a multiple of S bytes, so p is 16-byte aligned
+    const uint32_t rows = len >> 9;
+    uint32_t acc = 0;
+    const uint4 *p16 = reinterpret_cast<const uint4 *>(p) + lane;
+    uint32_t row = 0;
+    for (; row + 4 <= rows; row += 4) {
+      uint4 w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) w[u] = __ldcs(p16 + 32 * (row + u));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc = crc_op(op512, acc) ^ crc_raw16(tab, w[u]);
+    }
+    for (; row < rows; ++row) acc = crc_op(op512, acc) ^ crc_raw16(tab, __ldcs(p16 + 32 * row));
+    uint32_t r = rows ? crc_shift(ops, acc, (len - 512u * rows) + 496u - 16u * lane) : 0u;
+    // bytes after the full rows: lane j takes [16 j, 16 j + 16) of the rest
+    const uint32_t t = len - 512u * rows, t0 = 16u * lane;
+    if (t0 < t) {
+      const uint32_t tj = min(16u, t - t0);
+      uint32_t x = 0;
+      for (uint32_t k = 0; k < tj; ++k) x = (x >> 8) ^ tab[(x ^ p[512u * rows + t0 + k]) & 0xFFu];
+      r ^= crc_shift(ops, x, t - t0 - tj);
+    }
 #pragma unroll
     for (int d = 16; d; d >>= 1) r ^= __shfl_xor_sync(kFull, r, d);
-    if (lane == 0) seg_crc[i] = r ^ crc_shift(0xFFFFFFFFu, len) ^ 0xFFFFFFFFu;
+    if (lane == 0) seg_crc[i] = r;
   }
 }
 
-// one block per window: crc(window) from its pieces' CRCs
-__global__ void window_crc_kernel(const uint32_t *seg_crc, uint64_t lo, uint64_t hi, uint64_t window,
-                                  uint32_t log2_S, uint32_t *out) {
+// One block per window: the window's CRC from its pieces' raw CRCs. Thread t
+// folds a contiguous run of pieces, then a tree joins neighbouring runs.
+__global__ void __launch_bounds__(1024) window_crc_kernel(const uint32_t *seg_crc, uint64_t lo, uint64_t hi,
+                                                          uint64_t window, uint32_t log2_S, uint32_t *out) {
+  __shared__ uint32_t opS[1024];
   __shared__ uint32_t part[1024];
   __shared__ uint64_t plen[1024];
+  for (int i = threadIdx.x; i < 1024; i += blockDim.x) opS[i] = g_crc_tabs[4096 + 1024 * log2_S + i];
+  __syncthreads();
+  const uint32_t *gops = g_crc_tabs + 4096;
   const uint64_t k = blockIdx.x;
   const uint64_t wa = lo + k * window, wb = wa + window < hi ? wa + window : hi;
   const uint64_t first = lo >> log2_S;
@@ -608,18 +724,21 @@ __global__ void window_crc_kernel(const uint32_t *seg_crc, uint64_t lo, uint64_t
     const uint64_t s = s0 + i;
     const uint64_t a = (s << log2_S) > wa ? (s << log2_S) : wa;
     const uint64_t e = ((s + 1) << log2_S) < wb ? ((s + 1) << log2_S) : wb;
-    acc = crc_shift(acc, e - a) ^ seg_crc[s - first];
+    acc = (e - a == (uint64_t(1) << log2_S) ? crc_op(opS, acc) : crc_shift(gops, acc, e - a)) ^ seg_crc[s - first];
     alen += e - a;
   }
   part[threadIdx.x] = acc;
   plen[threadIdx.x] = alen;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t c = 0;
-    for (uint32_t t = 0; t < blockDim.x; ++t)
-      if (plen[t]) c = crc_shift(c, plen[t]) ^ part[t];
-    out[k] = c;
+  for (uint32_t d = 1; d < blockDim.x; d <<= 1) {
+    const uint32_t t = threadIdx.x;
+    if (t % (2 * d) == 0 && t + d < blockDim.x && plen[t + d]) {
+      part[t] = crc_shift(gops, part[t], plen[t + d]) ^ part[t + d];
+      plen[t] += plen[t + d];
+    }
+    __syncthreads();
   }
+  if (threadIdx.x == 0) out[k] = part[0] ^ crc_shift(gops, 0xFFFFFFFFu, plen[0]) ^ 0xFFFFFFFFu;
 }
 
 }  // namespace
@@ -705,32 +824,46 @@ cudaError_t launch_set_pages(uint32_t *page, const WorkItem *work, uint32_t n, c
 
 static bool g_crc_ready[64] = {};
 
+// Fills g_crc_tabs on the current device (once per device).
 static cudaError_t ensure_crc_constants() {
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && g_crc_ready[dev]) return cudaSuccess;
-  uint32_t tab[256];
-  for (uint32_t b = 0; b < 256; ++b) {
-    uint32_t c = b;
-    for (int k = 0; k < 8; ++k) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
-    tab[b] = c;
-  }
-  // op[0]: one zero byte; column i = register 1<<i advanced by 8 zero bits
-  static uint32_t op[48][32];
-  for (int i = 0; i < 32; ++i) {
-    uint32_t c = 1u << i;
-    for (int k = 0; k < 8; ++k) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
-    op[0][i] = c;
-  }
-  for (int k = 1; k < 48; ++k)
-    for (int i = 0; i < 32; ++i) {
-      uint32_t v = op[k - 1][i], r = 0;
-      for (int j = 0; j < 32; ++j)
-        if (v >> j & 1u) r ^= op[k - 1][j];
-      op[k][i] = r;
-    }
-  cudaError_t e = cudaMemcpyToSymbol(c_crc_table, tab, sizeof(tab));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_shift_op, op, sizeof(op));
+  static std::vector<uint32_t> tabs;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    tabs.assign(kCrcTabWords, 0);
+    auto byte_step = [](uint32_t c) {
+      for (int k = 0; k < 8; ++k) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+      return c;
+    };
+    uint32_t *T = tabs.data();
+    for (uint32_t b = 0; b < 256; ++b) T[b] = byte_step(b);
+    for (int k = 1; k < 16; ++k)
+      for (uint32_t b = 0; b < 256; ++b) {
+        const uint32_t c = T[256 * (k - 1) + b];
+        T[256 * k + b] = (c >> 8) ^ T[c & 0xFFu];
+      }
+    // col[k][i]: register 1 << i shifted by 2^k zero bytes (repeated squaring)
+    std::vector<uint32_t> col(32 * kCrcOps);
+    for (int i = 0; i < 32; ++i) col[i] = byte_step(1u << i);
+    for (int k = 1; k < kCrcOps; ++k)
+      for (int i = 0; i < 32; ++i) {
+        uint32_t v = col[32 * (k - 1) + i], r = 0;
+        for (int j = 0; j < 32; ++j)
+          if (v >> j & 1u) r ^= col[32 * (k - 1) + j];
+        col[32 * k + i] = r;
+      }
+    for (int k = 0; k < kCrcOps; ++k)
+      for (int i = 0; i < 4; ++i)
+        for (uint32_t v = 0; v < 256; ++v) {
+          uint32_t r = 0;
+          for (int j = 0; j < 8; ++j)
+            if (v >> j & 1u) r ^= col[32 * k + 8 * i + j];
+          T[4096 + 1024 * k + 256 * i + v] = r;
+        }
+  });
+  cudaError_t e = cudaMemcpyToSymbol(g_crc_tabs, tabs.data(), tabs.size() * sizeof(uint32_t));
   if (e == cudaSuccess && dev >= 0 && dev < 64) g_crc_ready[dev] = true;
   return e;
 }
@@ -741,10 +874,14 @@ cudaError_t launch_window_crc(OutView v, uint64_t lo, uint64_t hi, uint64_t wind
   cudaError_t e = ensure_crc_constants();
   if (e != cudaSuccess) return e;
   const uint64_t nseg = ((hi - 1) >> log2_S) - (lo >> log2_S) + 1;
-  int grid = (int)((nseg + 7) / 8 < 65535 ? (nseg + 7) / 8 : 65535);
-  seg_crc_kernel<<<grid, 256, 0, st>>>(v, log2_S, lo, hi, seg_crc);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t want = (nseg + kCrcThreads / 32 - 1) / (kCrcThreads / 32);
+  const int grid = (int)(want < (uint64_t)(3 * sms) ? want : (uint64_t)(3 * sms));
+  seg_crc_kernel<<<grid, kCrcThreads, 0, st>>>(v, log2_S, lo, hi, seg_crc);
   const uint64_t nwin = (hi - lo + window - 1) / window;
-  window_crc_kernel<<<(unsigned)nwin, 256, 0, st>>>(seg_crc, lo, hi, window, log2_S, crc);
+  window_crc_kernel<<<(unsigned)nwin, 1024, 0, st>>>(seg_crc, lo, hi, window, log2_S, crc);
   return cudaGetLastError();
 }
 

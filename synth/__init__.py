@@ -57,6 +57,7 @@ def _load():
             lib.synth_uniform.argtypes = [u64, u64, u64, u64, u64p]
             lib.synth_bytes.argtypes = [u64, u64, u64, u8p, ctypes.c_int, u8p]
             lib.synth_poisson_gaps.argtypes = [u64, u64, u64, ctypes.c_double, u64p]
+            lib.synth_qualities.argtypes = [u64, u64, u64, u64, u8p]
             _lib = lib
     return _lib
 
@@ -188,6 +189,15 @@ def random_bytes(seed_a: int, seed_b: int, n: int, alphabet: bytes = bytes(range
     out = np.empty(n, dtype=np.uint8)
     alpha = np.frombuffer(alphabet, dtype=np.uint8).copy()
     lib.synth_bytes(seed_a, seed_b, n, _p8(alpha), len(alphabet), _p8(out))
+    return out
+
+
+def qualities(n: int, seed: int = 6, read_len: int = 150) -> np.ndarray:
+    """n bytes of back-to-back Phred+33 quality strings (the FASTQ quality
+    model) with nothing between them: a literal-only symbol stream."""
+    lib = _load()
+    out = np.empty(n, dtype=np.uint8)
+    lib.synth_qualities(seed, 0, n, read_len, _p8(out))
     return out
 
 

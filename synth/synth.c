@@ -591,6 +591,14 @@ void synth_bytes(uint64_t seed_a, uint64_t seed_b, uint64_t n, const uint8_t *al
   for (uint64_t i = 0; i < n; ++i) out[i] = alphabet[rng_below(&r, (uint64_t)k)];
 }
 
+/* n bytes of back-to-back quality strings of read_len symbols each (the FASTQ
+ * quality model above), with no headers, bases or newlines */
+void synth_qualities(uint64_t seed_a, uint64_t seed_b, uint64_t n, uint64_t read_len, uint8_t *out) {
+  rng_t r;
+  rng_seed(&r, seed_a ^ 0x9A1ull, seed_b);
+  for (uint64_t at = 0; at < n; at += read_len) read_qual(&r, n - at < read_len ? n - at : read_len, out + at);
+}
+
 /* exponential inter-arrival gaps (Poisson process), in nanoseconds, rate per second */
 void synth_poisson_gaps(uint64_t seed_a, uint64_t seed_b, uint64_t n, double rate, uint64_t *out) {
   rng_t r;

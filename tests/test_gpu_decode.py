@@ -183,14 +183,18 @@ def test_read_lookup_then_decode():
 
 # -------------------------------------------------------------- ring streaming
 
-@pytest.mark.parametrize("lo", [0, 3 << 14])
-def test_stream_range_crcs(lo):
+@pytest.mark.parametrize("log2_B,lo,cut", [(14, 0, 0), (14, 3 << 14, 0), (14, 0, 16384 - 515), (8, 0, 0),
+                                            (8, 256 * 5, 37)])
+def test_stream_range_crcs(log2_B, lo, cut):
+    """Per-window CRC-32 of ring streaming equals zlib on the source bytes, for
+    16 KiB segments (row-strided hashing), 256-byte segments (per-lane tails
+    only) and ends that cut the last segment short."""
     d = synth.fasta(5_000_000, seed=12, n_chrom=3)
     D = 1 << 18
-    a = ace.encode(d, dist_bound=D, min_match=12)
+    a = ace.encode(d, log2_B=log2_B, dist_bound=D, min_match=12)
     window = 1 << 19
     ring = 1 << 21
-    hi = d.size
+    hi = d.size - cut
     with ace.Archive(a) as arc:
         nw = (hi - lo + window - 1) // window
         crc = torch.zeros(nw, dtype=torch.int32, device="cuda")
