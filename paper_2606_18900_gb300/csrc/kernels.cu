@@ -100,20 +100,20 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
   return v;
 }
 
-// Wait until every lane with `need` sees *flag == epoch. False on timeout or
-// when another warp has latched an error.
-__device__ bool wait_flags(const uint32_t *flag, bool need, uint32_t epoch, uint64_t deadline, uint32_t *err,
-                           int lane) {
-  for (uint32_t spin = 0;; ++spin) {
-    bool ok = !need || ld_acquire(flag) == epoch;
-    if (__all_sync(kFull, ok)) return true;
-    if (ld_relaxed(err) != 0) return false;
-    if (now_ns() > deadline) {
-      if (lane == 0) latch(err, kErrTimeout);
-      return false;
-    }
-    __nanosleep(spin < 16 ? 32 : 256);
+// The warp's next work index (lane 0's atomic on counter) and whether the
+// error word is set, both read by lane 0 and broadcast, so that every lane
+// takes the same branch: lanes that read the error word themselves could see
+// different values while another warp latches it, and a warp whose lanes part
+// there would meet at different warp-synchronous calls.
+__device__ __forceinline__ uint32_t take_item(uint32_t *counter, const uint32_t *err, int lane, bool &failed) {
+  uint32_t idx = 0, e = 0;
+  if (lane == 0) {
+    idx = atomicAdd(counter, 1u);
+    e = ld_relaxed(err);
   }
+  idx = __shfl_sync(kFull, idx, 0);
+  failed = __shfl_sync(kFull, e, 0) != 0;
+  return idx;
 }
 
 // u16 little-endian at p (2-byte aligned)
@@ -156,10 +156,9 @@ struct MatchTable {
 
 // Decode one segment into view V and publish its ready flag.
 //
-// lut: the 4 x 4096-entry decode table (shared or global memory). sstage /
-// scap: the warp's shared-memory staging area and its size; gstage: the warp's
-// 16 KiB global staging slot, used when the command streams do not fit scap.
-// mt: the warp's shared match table; ring: the warp's 512-word shared ring.
+// lut: the 4 x 4096-entry decode table (shared or global memory). d: the
+// segment's directory record. mt: the warp's shared match table; ring: the
+// warp's 512-word shared ring.
 //
 // Phases: (1) rANS over the three command classes into staging; (2) parse,
 // scans and every rule check, rewriting each command's literal-run and
@@ -170,19 +169,21 @@ struct MatchTable {
 // rounds: a round copies every pending match of a 32-command chunk whose
 // source does not overlap the output of an earlier pending match, the bytes
 // of the round spread over all lanes; (5) publish.
-template <bool kSmemLut, int kMode>
-__device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevArchive &A, const OutView &V,
-                                               uint32_t seg, uint32_t epoch, const uint32_t *lut, uint8_t *sstage,
-                                               uint32_t scap, uint8_t *gstage, MatchTable *mt, uint16_t *ring,
-                                               int lane) {
+//
+// stage: the warp's staging area for the command streams; kSharedStage says
+// it is the shared-memory one (so its accesses compile to shared loads and
+// stores), else it is the global slot.
+template <bool kSmemLut, int kMode, bool kSharedStage>
+__device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const DevArchive &A, const OutView &V,
+                                                    uint32_t seg, const SegRec &d, uint32_t epoch,
+                                                    const uint32_t *lut, uint8_t *stage, MatchTable *mt,
+                                                    uint16_t *ring, int lane) {
   const uint32_t log2_S = A.log2_S;
   const uint64_t seg_start = (uint64_t)seg << log2_S;
   const uint64_t rem = A.n - seg_start;
   const uint32_t out_size = rem < (uint64_t(1) << log2_S) ? (uint32_t)rem : (1u << log2_S);
-  const SegRec d = A.dir[seg];
   const uint32_t nc = d.n_cmd, nl = d.n_lit, nw = d.n_words, W = A.W;
   const uint32_t b1 = 2 * nc, b2 = 4 * nc, b3 = (4 + W) * nc, n_sym = b3 + nl;
-  uint8_t *stage = b3 <= scap ? sstage : gstage;
   // the segment's own output is contiguous in every view
   uint8_t *const out = at(V, seg_start, log2_S);
   bool ok = out != nullptr;
@@ -350,26 +351,55 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
   if (!__all_sync(kFull, x == kRansL) || wp != nw) ok = false;
   __syncwarp();
 
-  // (4) matches
+  // (4) matches. First wait until every source segment of the segment's
+  // matches has published its flag: all flags are polled with relaxed loads
+  // (independent, so they overlap), then one fence orders the source reads
+  // after the observed releases. The wait is bounded.
   const uint64_t deadline = now_ns() + L.wait_ns;
+  auto cmd_src = [&](uint32_t c) {
+    uint64_t v = 0;
+    for (uint32_t b = 0; b < W; ++b) v |= (uint64_t)stage[b2 + W * c + b] << (8 * b);
+    return v;
+  };
+  auto cmd_len = [&](uint32_t c) {
+    return (c + 1 < nc ? ld16(stage + b1 + 2 * c + 2) : tot_m) - ld16(stage + b1 + 2 * c);
+  };
+  if (ok && nc) {
+    bool mine = false;
+    for (uint32_t spin = 0;; ++spin) {
+      if (!mine) {
+        mine = true;
+        for (uint32_t c = lane; c < nc; c += 32) {
+          const uint64_t src = cmd_src(c);
+          const uint64_t q0 = src >> log2_S, q1 = (src + cmd_len(c) - 1) >> log2_S;
+          if (q0 != seg && ld_relaxed(A.flags + q0) != epoch) mine = false;
+          if (q1 != q0 && q1 != seg && ld_relaxed(A.flags + q1) != epoch) mine = false;
+        }
+      }
+      if (__all_sync(kFull, mine)) break;
+      // give up when another warp has latched an error or at the deadline;
+      // lane 0 decides for the warp
+      uint32_t why = 0;
+      if (lane == 0) why = ld_relaxed(L.err) != 0 ? 1u : now_ns() > deadline ? 2u : 0u;
+      why = __shfl_sync(kFull, why, 0);
+      if (why) {
+        if (why == 2 && lane == 0) latch(L.err, kErrTimeout);
+        ok = false;
+        break;
+      }
+      __nanosleep(spin < 16 ? 32 : 256);
+    }
+    __threadfence();
+  }
   for (uint32_t c0 = 0; ok && c0 < nc; c0 += 32) {
     const uint32_t c = c0 + lane;
     const bool valid = c < nc;
     uint32_t ml = 0;
     uint64_t src = 0, dst = ~uint64_t(0);
     if (valid) {
-      const uint32_t msum = ld16(stage + b1 + 2 * c);
-      ml = (c + 1 < nc ? ld16(stage + b1 + 2 * c + 2) : tot_m) - msum;
-      dst = seg_start + ld16(stage + 2 * c) + msum;
-      for (uint32_t b = 0; b < W; ++b) src |= (uint64_t)stage[b2 + W * c + b] << (8 * b);
-    }
-    const uint64_t q0 = src >> log2_S, q1 = valid ? (src + ml - 1) >> log2_S : q0;
-    const bool need0 = valid && q0 != seg;
-    const bool need1 = valid && q1 != q0 && q1 != seg;
-    if (!wait_flags(A.flags + (need0 ? q0 : 0), need0, epoch, deadline, L.err, lane) ||
-        !wait_flags(A.flags + (need1 ? q1 : 0), need1, epoch, deadline, L.err, lane)) {
-      ok = false;
-      break;
+      ml = cmd_len(c);
+      dst = seg_start + ld16(stage + 2 * c) + ld16(stage + b1 + 2 * c);
+      src = cmd_src(c);
     }
     mt->src[lane] = src;
     mt->dst[lane] = dst;
@@ -419,40 +449,62 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
       mt->len[lane] = ml;
       if (lane == 31) mt->start[32] = incl;
       __syncwarp();
-      for (uint32_t uu = lane; uu < total; uu += 32) {
+      auto unit_match = [&](uint32_t uu) {
         uint32_t m = 0;
 #pragma unroll
         for (int st = 16; st; st >>= 1)
           if (mt->start[m + st] <= uu) m += st;
-        if (vec) {
+        return m;
+      };
+      if (vec) {
+        // two units per lane per iteration, both units' loads issued before
+        // either store (sources of a round never overlap its outputs)
+        struct Unit {
+          uint8_t *to;
+          uint32_t o, n, c;
+          uint4 X, Y;
+        };
+        auto prep = [&](uint32_t uu, Unit &u) {
+          const uint32_t m = unit_match(uu);
           const uint32_t doff = (uint32_t)(mt->dst[m] - seg_start);
           const uint32_t b16 = (doff & ~15u) + ((uu - mt->start[m]) << 4);
           const uint32_t a0 = max(doff, b16), a1 = min(doff + mt->len[m], b16 + 16);
-          const uint32_t o = a0 - b16, n = a1 - a0;
+          u.o = a0 - b16;
+          u.n = a1 - a0;
+          u.to = out + b16;
           const uint64_t P = mt->src[m] + (a0 - doff);
           const uint8_t *pa = src_at<kMode>(V, P, log2_S);
           const uint32_t dl = (uint32_t)reinterpret_cast<uintptr_t>(pa) & 15u;
-          uint4 X = make_uint4(0, 0, 0, 0), Y = X;
-          uint32_t c;
-          if (dl >= o) {
-            X = *reinterpret_cast<const uint4 *>(pa - dl);
-            if (dl + n > 16) Y = *reinterpret_cast<const uint4 *>(src_at<kMode>(V, P + (16 - dl), log2_S));
-            c = dl - o;
+          u.X = make_uint4(0, 0, 0, 0);
+          u.Y = u.X;
+          if (dl >= u.o) {
+            u.X = *reinterpret_cast<const uint4 *>(pa - dl);
+            if (dl + u.n > 16) u.Y = *reinterpret_cast<const uint4 *>(src_at<kMode>(V, P + (16 - dl), log2_S));
+            u.c = dl - u.o;
           } else {
-            Y = *reinterpret_cast<const uint4 *>(pa - dl);
-            c = 16 + dl - o;
+            u.Y = *reinterpret_cast<const uint4 *>(pa - dl);
+            u.c = 16 + dl - u.o;
           }
+        };
+        auto commit = [&](const Unit &u) {
           uint32_t r[4];
-          realign16(X, Y, c, r);
-          uint8_t *to = out + b16;
-          if (n == 16) {
-            *reinterpret_cast<uint4 *>(to) = make_uint4(r[0], r[1], r[2], r[3]);
+          realign16(u.X, u.Y, u.c, r);
+          if (u.n == 16) {
+            *reinterpret_cast<uint4 *>(u.to) = make_uint4(r[0], r[1], r[2], r[3]);
           } else {
 #pragma unroll
             for (uint32_t i = 0; i < 16; ++i)
-              if (i - o < n) to[i] = (uint8_t)(r[i >> 2] >> (8 * (i & 3)));
+              if (i - u.o < u.n) u.to[i] = (uint8_t)(r[i >> 2] >> (8 * (i & 3)));
           }
-        } else {
+        };
+        for (uint32_t uu = lane; uu < total; uu += 32) {
+          Unit ua;
+          prep(uu, ua);
+          commit(ua);
+        }
+      } else {
+        for (uint32_t uu = lane; uu < total; uu += 32) {
+          const uint32_t m = unit_match(uu);
           const uint32_t o = (uu - mt->start[m]) << 4;
           const uint32_t n = min(16u, mt->len[m] - o);
           const uint64_t p = mt->src[m] + o;
@@ -478,6 +530,31 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
   if (lane == 0 && ok && !(A.blocked && A.blocked[seg])) st_release(A.flags + seg, epoch);
 }
 
+// The rare path with globally staged command streams is a call of its own, so
+// that it does not share the register allocation of the inlined shared path.
+template <bool kSmemLut, int kMode>
+__device__ __noinline__ void decode_segment_gstage(const DecodeLaunch &L, const DevArchive &A, const OutView &V,
+                                                   uint32_t seg, const SegRec &d, uint32_t epoch,
+                                                   const uint32_t *lut, uint8_t *gstage, MatchTable *mt,
+                                                   uint16_t *ring, int lane) {
+  decode_segment_impl<kSmemLut, kMode, false>(L, A, V, seg, d, epoch, lut, gstage, mt, ring, lane);
+}
+
+// Decode one segment (see decode_segment_impl): command streams of at most
+// scap bytes are staged in the warp's shared area sstage, larger ones in its
+// global slot gstage.
+template <bool kSmemLut, int kMode>
+__device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevArchive &A, const OutView &V,
+                                               uint32_t seg, uint32_t epoch, const uint32_t *lut, uint8_t *sstage,
+                                               uint32_t scap, uint8_t *gstage, MatchTable *mt, uint16_t *ring,
+                                               int lane) {
+  const SegRec d = A.dir[seg];
+  if ((4 + A.W) * d.n_cmd <= scap)
+    decode_segment_impl<kSmemLut, kMode, true>(L, A, V, seg, d, epoch, lut, sstage, mt, ring, lane);
+  else
+    decode_segment_gstage<kSmemLut, kMode>(L, A, V, seg, d, epoch, lut, gstage, mt, ring, lane);
+}
+
 // Persistent decode of one archive: its decode table is copied to shared
 // memory once per CTA, and every warp takes the next work item.
 // kMode: how the view maps positions (linear output, ring, or page table).
@@ -501,11 +578,10 @@ __global__ void __launch_bounds__(kDecodeThreads, 1) decode_kernel(DecodeLaunch 
   uint8_t *gstage = L.scratch + (size_t)gwarp * kStageBytes;
   const uint32_t epoch = ld_relaxed(L.epoch);
   for (;;) {
-    uint32_t idx = 0;
-    if (lane == 0) idx = atomicAdd(L.counter, 1u);
-    idx = __shfl_sync(kFull, idx, 0);
+    bool failed;
+    const uint32_t idx = take_item(L.counter, L.err, lane, failed);
     if (idx >= L.n_work) break;
-    if (ld_relaxed(L.err) != 0) continue;  // drain the list quickly after an error
+    if (failed) continue;  // drain the list quickly after an error
     decode_segment<true, kMode>(L, L.arc0, L.view0, L.work[idx].seg, epoch, slut, sstage, L.stage_cap, gstage, mt,
                                 ring, lane);
   }
@@ -545,11 +621,10 @@ __global__ void __launch_bounds__(kDecodeThreads, 1) batch_kernel(DecodeLaunch L
     for (uint32_t i = threadIdx.x; i < kLutBytes / 16; i += blockDim.x) s4[i] = g[i];
     __syncthreads();
     for (; (uint32_t)wid < L.active_warps;) {
-      uint32_t idx = 0;
-      if (lane == 0) idx = atomicAdd(&s_next, 1u);
-      idx = __shfl_sync(kFull, idx, 0);
+      bool failed;
+      const uint32_t idx = take_item(&s_next, L.err, lane, failed);
       if (idx >= A.n_seg) break;
-      if (ld_relaxed(L.err) != 0) continue;
+      if (failed) continue;
       decode_segment<true, kViewLinear>(L, A, s_V, A.order[idx].seg, epoch, slut, sstage, L.stage_cap, gstage, mt,
                                         ring, lane);
     }
@@ -972,11 +1047,10 @@ __global__ void __launch_bounds__(256) noalloc_decode_kernel(DecodeLaunch L, uin
   const uint32_t empty = reinterpret_cast<const uint32_t *>(g_noalloc_scratch)[kCtlEmpty / 4];
   const DevArchive &A = L.arc0;
   for (;;) {
-    uint32_t seg = 0;
-    if (lane == 0) seg = atomicAdd(L.counter, 1u);
-    seg = __shfl_sync(kFull, seg, 0);
+    bool failed;
+    const uint32_t seg = take_item(L.counter, L.err, lane, failed);
     if (seg >= A.n_seg) break;
-    if (ld_relaxed(L.err) != 0) continue;
+    if (failed) continue;
     // the directory was not validated on the host: check what the shared
     // segment decoder relies on before calling it
     const SegRec d = A.dir[seg];
