@@ -100,6 +100,25 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
   return v;
 }
 
+// Wait until every lane with `need` sees *flag == epoch. False on timeout or
+// when another warp has latched an error. Lane 0 reads the error word and
+// the clock and decides for the warp (see take_item).
+__device__ bool wait_flags(const uint32_t *flag, bool need, uint32_t epoch, uint64_t deadline, uint32_t *err,
+                           int lane) {
+  for (uint32_t spin = 0;; ++spin) {
+    bool ok = !need || ld_acquire(flag) == epoch;
+    if (__all_sync(kFull, ok)) return true;
+    uint32_t why = 0;
+    if (lane == 0) why = ld_relaxed(err) != 0 ? 1u : now_ns() > deadline ? 2u : 0u;
+    why = __shfl_sync(kFull, why, 0);
+    if (why) {
+      if (why == 2 && lane == 0) latch(err, kErrTimeout);
+      return false;
+    }
+    __nanosleep(spin < 8 ? 64 : spin < 32 ? 256 : 1024);
+  }
+}
+
 // The warp's next work index (lane 0's atomic on counter) and whether the
 // error word is set, both read by lane 0 and broadcast, so that every lane
 // takes the same branch: lanes that read the error word themselves could see
@@ -156,9 +175,10 @@ struct MatchTable {
 
 // Decode one segment into view V and publish its ready flag.
 //
-// lut: the 4 x 4096-entry decode table (shared or global memory). d: the
-// segment's directory record. mt: the warp's shared match table; ring: the
-// warp's 512-word shared ring.
+// lut: the 4 x 4096-entry decode table (shared or global memory). sstage /
+// scap: the warp's shared-memory staging area and its size; gstage: the warp's
+// 16 KiB global staging slot, used when the command streams do not fit scap.
+// mt: the warp's shared match table; ring: the warp's 512-word shared ring.
 //
 // Phases: (1) rANS over the three command classes into staging; (2) parse,
 // scans and every rule check, rewriting each command's literal-run and
@@ -169,21 +189,19 @@ struct MatchTable {
 // rounds: a round copies every pending match of a 32-command chunk whose
 // source does not overlap the output of an earlier pending match, the bytes
 // of the round spread over all lanes; (5) publish.
-//
-// stage: the warp's staging area for the command streams; kSharedStage says
-// it is the shared-memory one (so its accesses compile to shared loads and
-// stores), else it is the global slot.
-template <bool kSmemLut, int kMode, bool kSharedStage>
-__device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const DevArchive &A, const OutView &V,
-                                                    uint32_t seg, const SegRec &d, uint32_t epoch,
-                                                    const uint32_t *lut, uint8_t *stage, MatchTable *mt,
-                                                    uint16_t *ring, int lane) {
+template <bool kSmemLut, int kMode>
+__device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevArchive &A, const OutView &V,
+                                               uint32_t seg, uint32_t epoch, const uint32_t *lut, uint8_t *sstage,
+                                               uint32_t scap, uint8_t *gstage, MatchTable *mt, uint16_t *ring,
+                                               int lane) {
   const uint32_t log2_S = A.log2_S;
   const uint64_t seg_start = (uint64_t)seg << log2_S;
   const uint64_t rem = A.n - seg_start;
   const uint32_t out_size = rem < (uint64_t(1) << log2_S) ? (uint32_t)rem : (1u << log2_S);
+  const SegRec d = A.dir[seg];
   const uint32_t nc = d.n_cmd, nl = d.n_lit, nw = d.n_words, W = A.W;
   const uint32_t b1 = 2 * nc, b2 = 4 * nc, b3 = (4 + W) * nc, n_sym = b3 + nl;
+  uint8_t *stage = b3 <= scap ? sstage : gstage;
   // the segment's own output is contiguous in every view
   uint8_t *const out = at(V, seg_start, log2_S);
   bool ok = out != nullptr;
@@ -351,88 +369,61 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
   if (!__all_sync(kFull, x == kRansL) || wp != nw) ok = false;
   __syncwarp();
 
-  // (4) matches. First wait until every source segment of the segment's
-  // matches has published its flag: all flags are polled with relaxed loads
-  // (independent, so they overlap), then one fence orders the source reads
-  // after the observed releases. The wait is bounded.
+  // (4) matches
   const uint64_t deadline = now_ns() + L.wait_ns;
-  auto cmd_src = [&](uint32_t c) {
-    uint64_t v = 0;
-    for (uint32_t b = 0; b < W; ++b) v |= (uint64_t)stage[b2 + W * c + b] << (8 * b);
-    return v;
-  };
-  auto cmd_len = [&](uint32_t c) {
-    return (c + 1 < nc ? ld16(stage + b1 + 2 * c + 2) : tot_m) - ld16(stage + b1 + 2 * c);
-  };
-  if (ok && nc) {
-    bool mine = false;
-    for (uint32_t spin = 0;; ++spin) {
-      if (!mine) {
-        mine = true;
-        for (uint32_t c = lane; c < nc; c += 32) {
-          const uint64_t src = cmd_src(c);
-          const uint64_t q0 = src >> log2_S, q1 = (src + cmd_len(c) - 1) >> log2_S;
-          if (q0 != seg && ld_relaxed(A.flags + q0) != epoch) mine = false;
-          if (q1 != q0 && q1 != seg && ld_relaxed(A.flags + q1) != epoch) mine = false;
-        }
-      }
-      if (__all_sync(kFull, mine)) break;
-      // give up when another warp has latched an error or at the deadline;
-      // lane 0 decides for the warp
-      uint32_t why = 0;
-      if (lane == 0) why = ld_relaxed(L.err) != 0 ? 1u : now_ns() > deadline ? 2u : 0u;
-      why = __shfl_sync(kFull, why, 0);
-      if (why) {
-        if (why == 2 && lane == 0) latch(L.err, kErrTimeout);
-        ok = false;
-        break;
-      }
-      __nanosleep(spin < 16 ? 32 : 256);
-    }
-    __threadfence();
-  }
   for (uint32_t c0 = 0; ok && c0 < nc; c0 += 32) {
     const uint32_t c = c0 + lane;
     const bool valid = c < nc;
     uint32_t ml = 0;
     uint64_t src = 0, dst = ~uint64_t(0);
     if (valid) {
-      ml = cmd_len(c);
-      dst = seg_start + ld16(stage + 2 * c) + ld16(stage + b1 + 2 * c);
-      src = cmd_src(c);
+      const uint32_t msum = ld16(stage + b1 + 2 * c);
+      ml = (c + 1 < nc ? ld16(stage + b1 + 2 * c + 2) : tot_m) - msum;
+      dst = seg_start + ld16(stage + 2 * c) + msum;
+      for (uint32_t b = 0; b < W; ++b) src |= (uint64_t)stage[b2 + W * c + b] << (8 * b);
+    }
+    const uint64_t q0 = src >> log2_S, q1 = valid ? (src + ml - 1) >> log2_S : q0;
+    const bool need0 = valid && q0 != seg;
+    const bool need1 = valid && q1 != q0 && q1 != seg;
+    if (!wait_flags(A.flags + (need0 ? q0 : 0), need0, epoch, deadline, L.err, lane) ||
+        !wait_flags(A.flags + (need1 ? q1 : 0), need1, epoch, deadline, L.err, lane)) {
+      ok = false;
+      break;
     }
     mt->src[lane] = src;
     mt->dst[lane] = dst;
     __syncwarp();
+    // The earlier matches of this chunk whose outputs overlap this match's
+    // source: outputs are disjoint and ascending, so they are the lanes j with
+    // dst_j < src + ml and dst_j + ml_j > src, a contiguous range [jlo, jhi]
+    // found by two binary searches (offsets from the segment start; a source
+    // that ends before the segment overlaps nothing); all lie below this lane
+    // because src + ml <= dst.
+    uint32_t hmask = 0;
+    {
+      const uint64_t se = src + ml;
+      const uint32_t se_rel = valid && se > seg_start ? (uint32_t)(se - seg_start) : 0u;
+      const uint32_t s_rel = valid && src > seg_start ? (uint32_t)(src - seg_start) : 0u;
+      const uint32_t d_off = valid ? (uint32_t)(dst - seg_start) : 0xFFFFFFFFu;
+      const uint32_t d_end = valid ? d_off + ml : 0xFFFFFFFFu;
+      uint32_t jh = 0, jl = 0;
+#pragma unroll
+      for (int st = 16; st; st >>= 1) {
+        if (__shfl_sync(kFull, d_off, jh + st) < se_rel) jh += st;
+        if (__shfl_sync(kFull, d_end, jl + st) <= s_rel) jl += st;
+      }
+      const bool any_h = __shfl_sync(kFull, d_off, jh) < se_rel;  // some output starts before the source ends
+      const bool any_l = __shfl_sync(kFull, d_end, jl) <= s_rel;  // some output ends before the source starts
+      const uint32_t jlo = any_l ? jl + 1 : 0;
+      if (any_h && jlo <= jh) hmask = ((2u << jh) - 1u) & ~((1u << jlo) - 1u);
+    }
     bool pending = valid;
     for (int round = 0;; ++round) {
       const uint32_t pm = __ballot_sync(kFull, pending);
       if (!pm) break;
       // a match waits while its source overlaps the output of an earlier
-      // pending match; outputs are disjoint and ascending, so in the first
-      // round (all pending) only the last output starting before the end of
-      // the source can overlap it
-      bool haz = false;
-      if (round == 0) {
-        const uint64_t se = src + ml;
-        uint32_t j = 0;
-        bool any = false;
-#pragma unroll
-        for (int st = 16; st; st >>= 1) {
-          const uint64_t dp = __shfl_sync(kFull, dst, j + st);
-          if (dp < se) j += st;
-        }
-        const uint64_t dj = __shfl_sync(kFull, dst, j);
-        const uint32_t mj = __shfl_sync(kFull, ml, j);
-        any = dj < se && (uint32_t)lane > j;
-        haz = pending && any && dj + mj > src;
-      } else {
-        for (int j = 0; j < 32; ++j) {
-          const uint64_t dj = __shfl_sync(kFull, dst, j);
-          const uint32_t mj = __shfl_sync(kFull, ml, j);
-          if (j < lane && (pm >> j & 1u) && src < dj + mj && src + ml > dj) haz = true;
-        }
-      }
+      // pending match
+      const bool haz = (pm & hmask) != 0;
       const bool ready = pending && !haz;
       // Units: with vec, the 16-byte-aligned blocks of each match's output
       // (a block's source bytes span at most two aligned source blocks, read
@@ -449,62 +440,49 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
       mt->len[lane] = ml;
       if (lane == 31) mt->start[32] = incl;
       __syncwarp();
-      auto unit_match = [&](uint32_t uu) {
+      for (uint32_t uu = lane; uu < total; uu += 32) {
         uint32_t m = 0;
 #pragma unroll
         for (int st = 16; st; st >>= 1)
           if (mt->start[m + st] <= uu) m += st;
-        return m;
-      };
-      if (vec) {
-        // two units per lane per iteration, both units' loads issued before
-        // either store (sources of a round never overlap its outputs)
-        struct Unit {
-          uint8_t *to;
-          uint32_t o, n, c;
-          uint4 X, Y;
-        };
-        auto prep = [&](uint32_t uu, Unit &u) {
-          const uint32_t m = unit_match(uu);
+        if (vec) {
           const uint32_t doff = (uint32_t)(mt->dst[m] - seg_start);
           const uint32_t b16 = (doff & ~15u) + ((uu - mt->start[m]) << 4);
           const uint32_t a0 = max(doff, b16), a1 = min(doff + mt->len[m], b16 + 16);
-          u.o = a0 - b16;
-          u.n = a1 - a0;
-          u.to = out + b16;
+          const uint32_t o = a0 - b16, n = a1 - a0;
           const uint64_t P = mt->src[m] + (a0 - doff);
           const uint8_t *pa = src_at<kMode>(V, P, log2_S);
           const uint32_t dl = (uint32_t)reinterpret_cast<uintptr_t>(pa) & 15u;
-          u.X = make_uint4(0, 0, 0, 0);
-          u.Y = u.X;
-          if (dl >= u.o) {
-            u.X = *reinterpret_cast<const uint4 *>(pa - dl);
-            if (dl + u.n > 16) u.Y = *reinterpret_cast<const uint4 *>(src_at<kMode>(V, P + (16 - dl), log2_S));
-            u.c = dl - u.o;
+          uint4 X = make_uint4(0, 0, 0, 0), Y = X;
+          uint32_t c;
+          if (dl >= o) {
+            X = *reinterpret_cast<const uint4 *>(pa - dl);
+            if (dl + n > 16) Y = *reinterpret_cast<const uint4 *>(src_at<kMode>(V, P + (16 - dl), log2_S));
+            c = dl - o;
           } else {
-            u.Y = *reinterpret_cast<const uint4 *>(pa - dl);
-            u.c = 16 + dl - u.o;
+            Y = *reinterpret_cast<const uint4 *>(pa - dl);
+            c = 16 + dl - o;
           }
-        };
-        auto commit = [&](const Unit &u) {
           uint32_t r[4];
-          realign16(u.X, u.Y, u.c, r);
-          if (u.n == 16) {
-            *reinterpret_cast<uint4 *>(u.to) = make_uint4(r[0], r[1], r[2], r[3]);
+          realign16(X, Y, c, r);
+          uint8_t *to = out + b16;
+          if (n == 16) {
+            *reinterpret_cast<uint4 *>(to) = make_uint4(r[0], r[1], r[2], r[3]);
           } else {
+            // bytes [o, o + n) of the block: whole words with one store,
+            // the (at most three) bytes at each end one by one
 #pragma unroll
-            for (uint32_t i = 0; i < 16; ++i)
-              if (i - u.o < u.n) u.to[i] = (uint8_t)(r[i >> 2] >> (8 * (i & 3)));
+            for (uint32_t j = 0; j < 4; ++j) {
+              if (4 * j >= o && 4 * j + 4 <= o + n) {
+                *reinterpret_cast<uint32_t *>(to + 4 * j) = r[j];
+              } else if (4 * j + 4 > o && 4 * j < o + n) {
+#pragma unroll
+                for (uint32_t b = 0; b < 4; ++b)
+                  if (4 * j + b - o < n) to[4 * j + b] = (uint8_t)(r[j] >> (8 * b));
+              }
+            }
           }
-        };
-        for (uint32_t uu = lane; uu < total; uu += 32) {
-          Unit ua;
-          prep(uu, ua);
-          commit(ua);
-        }
-      } else {
-        for (uint32_t uu = lane; uu < total; uu += 32) {
-          const uint32_t m = unit_match(uu);
+        } else {
           const uint32_t o = (uu - mt->start[m]) << 4;
           const uint32_t n = min(16u, mt->len[m] - o);
           const uint64_t p = mt->src[m] + o;
@@ -528,31 +506,6 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
   __threadfence();
   __syncwarp();
   if (lane == 0 && ok && !(A.blocked && A.blocked[seg])) st_release(A.flags + seg, epoch);
-}
-
-// The rare path with globally staged command streams is a call of its own, so
-// that it does not share the register allocation of the inlined shared path.
-template <bool kSmemLut, int kMode>
-__device__ __noinline__ void decode_segment_gstage(const DecodeLaunch &L, const DevArchive &A, const OutView &V,
-                                                   uint32_t seg, const SegRec &d, uint32_t epoch,
-                                                   const uint32_t *lut, uint8_t *gstage, MatchTable *mt,
-                                                   uint16_t *ring, int lane) {
-  decode_segment_impl<kSmemLut, kMode, false>(L, A, V, seg, d, epoch, lut, gstage, mt, ring, lane);
-}
-
-// Decode one segment (see decode_segment_impl): command streams of at most
-// scap bytes are staged in the warp's shared area sstage, larger ones in its
-// global slot gstage.
-template <bool kSmemLut, int kMode>
-__device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevArchive &A, const OutView &V,
-                                               uint32_t seg, uint32_t epoch, const uint32_t *lut, uint8_t *sstage,
-                                               uint32_t scap, uint8_t *gstage, MatchTable *mt, uint16_t *ring,
-                                               int lane) {
-  const SegRec d = A.dir[seg];
-  if ((4 + A.W) * d.n_cmd <= scap)
-    decode_segment_impl<kSmemLut, kMode, true>(L, A, V, seg, d, epoch, lut, sstage, mt, ring, lane);
-  else
-    decode_segment_gstage<kSmemLut, kMode>(L, A, V, seg, d, epoch, lut, gstage, mt, ring, lane);
 }
 
 // Persistent decode of one archive: its decode table is copied to shared
