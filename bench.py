@@ -63,6 +63,20 @@ def parse():
     return p.parse_args()
 
 
+def recorded_traffic(key):
+    """DRAM bytes per launch recorded from an ncu capture (profiles/traffic.json),
+    or None when the kernel source changed since the capture."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        src = os.path.join(ROOT, "paper_2606_18900_gb300", "csrc", "kernels.cu")
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["kernels_cu_sha256"]:
+            return None
+        return rec[key]["traffic_bytes"]
+    except Exception:
+        return None
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -324,8 +338,10 @@ def workload_fastq(args):
         line = base_line(
             args, value, total_ms / args.steps, world, config,
             roofline={"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                      "peak_kind": peak_kind, "traffic": None, "kernel": "decode_kernel",
-                      "bytes_model": "C + U + M per launch"},
+                      "peak_kind": peak_kind, "kernel": "decode_kernel", "bytes_model": "C + U + M per launch",
+                      "traffic": (recorded_traffic("fastq_1gib_log2B14")
+                                  if size == 1 << 30 and args.log2_block == 14 and min_match == 16 else None),
+                      "algorithmic_bytes": C + U + M},
             random_read={"p50_ms": pctl(lat, 50), "p99_ms": pctl(lat, 99), "n": len(lat),
                          "what": "read_lookup + aceapex_decode_range of one FASTQ record, synchronous",
                          "bit_exact": reads_ok},
