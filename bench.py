@@ -334,7 +334,7 @@ def workload_fastq(args):
                   "log2_block": args.log2_block, "min_match": min_match, "ratio": round(N / arc_bytes.size, 3),
                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (archive and output > 126 MB)",
                   "C_bytes": C, "U_bytes": U, "M_bytes": M, "max_level": st["max_level"],
-                  "encode_seconds": round(enc_s, 2)}
+                  "level_histogram": arc.level_counts(), "encode_seconds": round(enc_s, 2)}
         line = base_line(
             args, value, total_ms / args.steps, world, config,
             roofline={"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -345,7 +345,8 @@ def workload_fastq(args):
             random_read={"p50_ms": pctl(lat, 50), "p99_ms": pctl(lat, 99), "n": len(lat),
                          "what": "read_lookup + aceapex_decode_range of one FASTQ record, synchronous",
                          "bit_exact": reads_ok},
-            cpu_baseline=cpu, e2e=e2e, gpu_launches=2 * args.steps, clocks=clk, bit_exact=ok)
+            cpu_baseline=cpu, e2e=e2e, gpu_launches=2 * args.steps, clocks=clk, bit_exact=ok,
+            ms_median=float(np.median(step_ms)))
         print(json.dumps(line), flush=True)
     arc.close()
     if world > 1:
@@ -454,7 +455,7 @@ def workload_entropy(args):
                                f"instructions per 32 symbols, {props.multi_processor_count} SMs x 4 schedulers x "
                                f"{mhz:.0f} MHz", "traffic": None, "kernel": "decode_kernel"},
                      hbm_frac=(C + U) / avg_s / 1e9 / peak_hbm, gpu_launches=2 * args.steps, clocks=clk,
-                     bit_exact=ok)
+                     bit_exact=ok, ms_median=float(np.median(step_ms)))
     print(json.dumps(line), flush=True)
 
 

@@ -79,6 +79,14 @@ uint64_t aceapex_decoded_size(const aceapex_archive *a);
 int aceapex_get_stats(const aceapex_archive *a, aceapex_stats *st);
 
 /*
+ * Histogram of the segments' dependency levels (the wavefront depth of paper
+ * §2's block DAG under the level cap of FORMAT.md §2): h_counts[l] = number of
+ * segments at level l, for l < n (levels >= n are not counted). Host only, no
+ * GPU work. Errors: EINVAL (NULL pointers).
+ */
+int aceapex_level_counts(const aceapex_archive *a, uint64_t *h_counts, uint32_t n);
+
+/*
  * Whole-file device-resident decode (paper §3.3, "v4": entropy decode and
  * match resolution both on the GPU, output kept in VRAM). Writes the N
  * decoded bytes to d_out[0..N). One persistent launch: each warp takes the

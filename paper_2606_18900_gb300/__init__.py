@@ -111,6 +111,7 @@ def lib():
             L.aceapex_decoded_size.argtypes = [vp]
             L.aceapex_decoded_size.restype = u64
             L.aceapex_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+            L.aceapex_level_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint32]
             L.aceapex_decode_all.argtypes = [vp, vp, u64, vp, ctypes.POINTER(Stats)]
             L.aceapex_decode_range.argtypes = [vp, u64, u64, vp, u64, vp]
             L.aceapex_read_lookup.argtypes = [vp, u64, u64p, u64p]
@@ -253,6 +254,13 @@ class Archive:
         st = Stats()
         _check(lib().aceapex_get_stats(self._h, ctypes.byref(st)), "aceapex_get_stats")
         return st.as_dict()
+
+    def level_counts(self) -> list:
+        """Number of segments at each dependency level 0 .. max_level."""
+        n = self.stats()["max_level"] + 1
+        h = (ctypes.c_uint64 * n)()
+        _check(lib().aceapex_level_counts(self._h, h, n), "aceapex_level_counts")
+        return [int(x) for x in h]
 
     def decode_all(self, out, stream=None):
         """Decode the whole archive into device buffer ``out`` (async)."""

@@ -382,6 +382,14 @@ void aceapex_close(aceapex_archive *a) {
 
 uint64_t aceapex_decoded_size(const aceapex_archive *a) { return a ? a->h.n : 0; }
 
+int aceapex_level_counts(const aceapex_archive *a, uint64_t *h_counts, uint32_t n) {
+  if (!a || (!h_counts && n)) return ACEAPEX_EINVAL;
+  for (uint32_t l = 0; l < n; ++l) h_counts[l] = 0;
+  for (const SegRec &r : a->dir)
+    if (r.level < n) h_counts[r.level]++;
+  return ACEAPEX_OK;
+}
+
 int aceapex_get_stats(const aceapex_archive *a, aceapex_stats *st) {
   if (!a || !st) return ACEAPEX_EINVAL;
   *st = a->stats;

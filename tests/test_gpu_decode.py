@@ -181,6 +181,14 @@ def test_read_lookup_then_decode():
             arc.read_lookup(2000)
 
 
+def test_level_counts_match_directory():
+    d = synth.pe_fastq(2 << 20, ref_len=500_000)
+    a = ace.encode(d, min_match=12, max_level=5)
+    lv = oracle.sections(a)["dir"]["level"]
+    with ace.Archive(a) as arc:
+        assert arc.level_counts() == np.bincount(lv, minlength=arc.stats()["max_level"] + 1).tolist()
+
+
 # -------------------------------------------------------------- ring streaming
 
 @pytest.mark.parametrize("log2_B,lo,cut", [(14, 0, 0), (14, 3 << 14, 0), (14, 0, 16384 - 515), (8, 0, 0),
