@@ -538,7 +538,8 @@ def workload_genome(args):
     gen_s = time.perf_counter() - t
     D = 1 << 30
     t = time.perf_counter()
-    arc_bytes = ace.encode(data, log2_B=args.log2_block, min_match=args.min_match or 32, dist_bound=D)
+    cidx, width = ace.fasta_index(data)  # chr:pos coordinate index, stored as the archive's read index
+    arc_bytes = ace.encode(data, log2_B=args.log2_block, min_match=args.min_match or 32, dist_bound=D, reads=cidx)
     enc_s = time.perf_counter() - t
     arc = ace.Archive(arc_bytes)
     st = arc.stats()
@@ -575,6 +576,45 @@ def workload_genome(args):
         if k < 64:
             reg_ok &= bytes(buf[:150].cpu().numpy()) == data[s0:s0 + 150].tobytes()
     arc.check(stream)
+    # the same region lookups by coordinates (record, position) through the
+    # coordinate index: bases only, newlines dropped on the device
+    n_rec = len(cidx) // 2
+    rec_end = [int(cidx[2 * k + 2]) if 2 * k + 2 < len(cidx) else N for k in range(n_rec)]
+    bases = [(e - int(cidx[2 * k + 1])) - (e - int(cidx[2 * k + 1]) + width) // (width + 1)
+             for k, e in enumerate(rec_end)]
+    rng = np.random.default_rng(41)
+    coord_lat, coord_ok = [], True
+    for k in range(min(args.regions, 10_000)):
+        chrom = int(rng.integers(0, n_rec))
+        if bases[chrom] < 150:
+            continue
+        p0 = int(rng.integers(0, bases[chrom] - 150))
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        arc.decode_region(chrom, p0, 150, buf, width, stream)
+        stream.synchronize()
+        coord_lat.append((time.perf_counter() - t) * 1e3)
+        if k < 64:
+            lo, hi = arc.region_lookup(chrom, p0, 150, width)
+            coord_ok &= bytes(buf[:150].cpu().numpy()) == data[lo:hi].tobytes().replace(b"\n", b"")
+    arc.check(stream)
+    # the same byte regions batched: all submitted at once to the serving
+    # engine, which decodes the union of their closures per batch
+    nb = min(args.regions, 20_000)
+    outs = torch.empty((nb, 160), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    with ace.Server([arc], mem_budget=8 << 30, slots=4) as srv:
+        t = time.perf_counter()
+        tickets = [srv.submit(0, int(s0), int(s0) + 150, outs[i]) for i, s0 in enumerate(starts[:nb])]
+        blat = [srv.wait(tk) for tk in tickets]
+        b_s = time.perf_counter() - t
+        bst = srv.stats()
+    b_ok = all(bytes(outs[i, :150].cpu().numpy()) == data[int(s0):int(s0) + 150].tobytes()
+               for i, s0 in enumerate(starts[:64]))
+    batched = {"regions_per_s": nb / b_s, "p50_ms": pctl(blat, 50), "p99_ms": pctl(blat, 99), "n": nb,
+               "batches": bst["batches"], "bit_exact": bool(b_ok),
+               "what": "all regions submitted at once to aceapex_server_submit (latency includes queueing)",
+               "serial_regions_per_s": 1e3 / float(np.mean(lat)) if lat else None}
     line = base_line(args, N / (ms * 1e-3) / 1e9, ms, 1,
                      {"workload": f"FASTA genome {N} bytes, D = 1 GiB, streamed through a {ring}-byte device ring "
                                   f"in {window}-byte windows with a CRC-32 per window",
@@ -586,7 +626,11 @@ def workload_genome(args):
                                "kernel": "decode_kernel (ring) + CRC kernels", "bytes_model": "C + U + M per stream"},
                      random_read={"p50_ms": pctl(lat, 50), "p99_ms": pctl(lat, 99), "n": len(lat),
                                   "what": "150-byte region, aceapex_decode_range, synchronous", "bit_exact": reg_ok},
-                     crc_windows_match=ok, gpu_launches=None, bit_exact=bool(ok and reg_ok))
+                     coordinate_region={"p50_ms": pctl(coord_lat, 50), "p99_ms": pctl(coord_lat, 99),
+                                        "n": len(coord_lat), "bit_exact": bool(coord_ok),
+                                        "what": "150 bases at (record, position), aceapex_decode_region, synchronous"},
+                     batched_regions=batched, crc_windows_match=ok, gpu_launches=args.steps * (1 + 3 * nw),
+                     bit_exact=bool(ok and reg_ok and coord_ok and b_ok))
     print(json.dumps(line), flush=True)
 
 

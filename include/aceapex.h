@@ -265,6 +265,41 @@ void aceapex_free(void *p);
  * writes at most cap entries to h_out and returns the total count. */
 uint64_t aceapex_fastq_index(const void *h_in, uint64_t n, uint64_t *h_out, uint64_t cap);
 
+/*
+ * FASTA coordinate index (the paper's chr:pos index, left there as future
+ * work, §4.1): for every record, the offset of its '>' and the offset of its
+ * first sequence byte, and one more entry (the offset of the last byte) when
+ * the file's last line has no newline; writes at most cap entries to h_out
+ * and returns the total count. *line_width (when not NULL) receives the
+ * length of the longest sequence line. Stored as an archive's read index (the
+ * h_reads of aceapex_encode), it serves aceapex_region_lookup and
+ * aceapex_decode_region.
+ */
+uint64_t aceapex_fasta_index(const void *h_in, uint64_t n, uint64_t *h_out, uint64_t cap, uint32_t *line_width);
+
+/*
+ * Coordinates to bytes: bases [pos, pos + len) of record `chrom` (0-based,
+ * in file order) of a FASTA archive carrying the coordinate index above,
+ * whose sequence lines hold line_width bases each: base p sits at byte
+ * seq_start + p + floor(p / line_width). Writes the byte range [*byte_lo,
+ * *byte_hi) that covers the bases (with the newlines between them). Host
+ * only, O(1). Errors: EINVAL (no coordinate index, len or line_width 0),
+ * ERANGE (chrom or the bases outside the record).
+ */
+int aceapex_region_lookup(const aceapex_archive *a, uint64_t chrom, uint64_t pos, uint64_t len, uint32_t line_width,
+                          uint64_t *byte_lo, uint64_t *byte_hi);
+
+/*
+ * Region decode by coordinates: writes exactly the len bases of
+ * aceapex_region_lookup (newlines dropped) to d_out[0 .. len): the covering
+ * segments and their source closure are decoded as in aceapex_decode_range,
+ * then a gather kernel skips the newline after every line_width bases.
+ * Errors: those of aceapex_region_lookup, ERANGE (out_cap < len), ENOMEM,
+ * ECUDA.
+ */
+int aceapex_decode_region(aceapex_archive *a, uint64_t chrom, uint64_t pos, uint64_t len, uint32_t line_width,
+                          void *d_out, uint64_t out_cap, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

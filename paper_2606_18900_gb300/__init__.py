@@ -142,6 +142,10 @@ def lib():
             L.aceapex_free.restype = None
             L.aceapex_fastq_index.argtypes = [vp, u64, u64p, u64]
             L.aceapex_fastq_index.restype = u64
+            L.aceapex_fasta_index.argtypes = [vp, u64, u64p, u64, ctypes.POINTER(ctypes.c_uint32)]
+            L.aceapex_fasta_index.restype = u64
+            L.aceapex_region_lookup.argtypes = [vp, u64, u64, u64, ctypes.c_uint32, u64p, u64p]
+            L.aceapex_decode_region.argtypes = [vp, u64, u64, u64, ctypes.c_uint32, vp, u64, vp]
             for f in ("aceapex_open", "aceapex_get_stats", "aceapex_decode_all", "aceapex_decode_range",
                       "aceapex_read_lookup", "aceapex_last_error", "aceapex_set_wait_limit",
                       "aceapex_debug_block_segments", "aceapex_stream_range", "aceapex_decode_batch",
@@ -212,6 +216,19 @@ def fastq_index(data) -> np.ndarray:
     return out[:n]
 
 
+def fasta_index(data):
+    """(coordinate index, line width) of a FASTA buffer: for every record the
+    offset of its '>' and of its first sequence byte."""
+    L = lib()
+    buf = _as_u8(data)
+    w = ctypes.c_uint32(0)
+    n = L.aceapex_fasta_index(buf.ctypes.data, buf.size, None, 0, None)
+    out = np.zeros(max(n, 1), dtype=np.uint64)
+    L.aceapex_fasta_index(buf.ctypes.data, buf.size, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), n,
+                          ctypes.byref(w))
+    return out[:n], int(w.value)
+
+
 # ------------------------------------------------------------------- archives
 
 class Archive:
@@ -276,6 +293,19 @@ class Archive:
         lo, hi = ctypes.c_uint64(), ctypes.c_uint64()
         _check(lib().aceapex_read_lookup(self._h, read_id, ctypes.byref(lo), ctypes.byref(hi)), "aceapex_read_lookup")
         return lo.value, hi.value
+
+    def region_lookup(self, chrom: int, pos: int, length: int, line_width: int = 60):
+        """Byte range covering bases [pos, pos + length) of FASTA record chrom."""
+        lo, hi = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().aceapex_region_lookup(self._h, chrom, pos, length, line_width, ctypes.byref(lo),
+                                           ctypes.byref(hi)), "aceapex_region_lookup")
+        return lo.value, hi.value
+
+    def decode_region(self, chrom: int, pos: int, length: int, out, line_width: int = 60, stream=None):
+        """Bases [pos, pos + length) of FASTA record chrom into out (newlines dropped)."""
+        cap = out.numel() * out.element_size()
+        _check(lib().aceapex_decode_region(self._h, chrom, pos, length, line_width, _ptr(out), cap,
+                                           _stream(stream)), "aceapex_decode_region")
 
     def stream_range(self, lo: int, hi: int, ring_bytes: int, window: int, crc_out, stream=None):
         _check(lib().aceapex_stream_range(self._h, lo, hi, ring_bytes, window, _ptr(crc_out), _stream(stream)),

@@ -605,4 +605,37 @@ uint64_t fastq_index(const uint8_t *in, uint64_t n, uint64_t *out, uint64_t cap)
   return k;
 }
 
+// FASTA coordinate index: for every record, the offset of its '>' and the
+// offset of its first sequence byte (the byte after the header line). The
+// line width is the longest first sequence line of any record (every line
+// of a record but its last has that length in a well-formed file). '>' only
+// starts headers, so the scan jumps from one '>' to the next with memchr.
+uint64_t fasta_index(const uint8_t *in, uint64_t n, uint64_t *out, uint64_t cap, uint32_t *line_width) {
+  uint64_t k = 0, width = 0;
+  for (uint64_t p = 0; p < n;) {
+    const void *g = std::memchr(in + p, '>', n - p);
+    if (!g) break;
+    const uint64_t q = static_cast<const uint8_t *>(g) - in;
+    p = q + 1;
+    if (q > 0 && in[q - 1] != '\n') continue;  // not at a line start
+    const void *e = std::memchr(in + q, '\n', n - q);
+    if (!e) break;  // a header without a sequence line
+    const uint64_t seq = static_cast<const uint8_t *>(e) - in + 1;
+    if (k < cap) out[k] = q;
+    if (k + 1 < cap) out[k + 1] = seq;
+    k += 2;
+    const void *l = seq < n ? std::memchr(in + seq, '\n', n - seq) : nullptr;
+    if (l) width = std::max<uint64_t>(width, static_cast<const uint8_t *>(l) - in - seq);
+    p = seq;
+  }
+  // a file whose last line has no newline gets one more entry, the offset of
+  // its last byte, so that lookups know the last line is not terminated
+  if (k >= 2 && n > 0 && in[n - 1] != '\n' && (k > cap || n - 1 > out[k - 1])) {
+    if (k < cap) out[k] = n - 1;
+    ++k;
+  }
+  if (line_width) *line_width = (uint32_t)width;
+  return k;
+}
+
 }  // namespace aceapex

@@ -18,6 +18,7 @@ namespace aceapex {
 int encode_archive(const uint8_t *in, uint64_t n, uint32_t log2_B, uint32_t min_match, uint32_t cap, uint64_t D,
                    const uint64_t *reads, uint64_t n_reads, int threads, uint8_t **out, uint64_t *out_len);
 uint64_t fastq_index(const uint8_t *in, uint64_t n, uint64_t *out, uint64_t cap);
+uint64_t fasta_index(const uint8_t *in, uint64_t n, uint64_t *out, uint64_t cap, uint32_t *line_width);
 }  // namespace aceapex
 
 using namespace aceapex;
@@ -441,6 +442,50 @@ int aceapex_read_lookup(const aceapex_archive *a, uint64_t read_id, uint64_t *by
   return ACEAPEX_OK;
 }
 
+int aceapex_region_lookup(const aceapex_archive *a, uint64_t chrom, uint64_t pos, uint64_t len, uint32_t line_width,
+                          uint64_t *byte_lo, uint64_t *byte_hi) {
+  if (!a || !byte_lo || !byte_hi || line_width == 0 || len == 0) return ACEAPEX_EINVAL;
+  const uint64_t n_idx = a->h.n_reads, n_rec = n_idx / 2;
+  if (n_rec == 0) return ACEAPEX_EINVAL;  // not a coordinate index
+  if (chrom >= n_rec) return ACEAPEX_ERANGE;
+  const uint64_t seq = a->reads[2 * chrom + 1];
+  const bool last_rec = chrom + 1 == n_rec;
+  const uint64_t end = last_rec ? a->h.n : a->reads[2 * chrom + 2];
+  if (end < seq) return ACEAPEX_ECORRUPT;
+  // B bases in lines of line_width, each line ending in a newline, take
+  // B + ceil(B / line_width) bytes; when the file's last line has no
+  // newline (an odd entry count marks it), the last record takes
+  // B + floor(B / line_width) bytes, less one if B is a whole number of lines
+  const uint64_t bytes = end - seq;
+  const uint64_t bases = last_rec && (n_idx & 1) ? bytes - bytes / (line_width + 1)
+                                             : bytes - (bytes + line_width) / (line_width + 1);
+  if (pos >= bases || len > bases - pos) return ACEAPEX_ERANGE;
+  const uint64_t last = pos + len - 1;
+  *byte_lo = seq + pos + pos / line_width;
+  *byte_hi = seq + last + last / line_width + 1;
+  return ACEAPEX_OK;
+}
+
+int aceapex_decode_region(aceapex_archive *a, uint64_t chrom, uint64_t pos, uint64_t len, uint32_t line_width,
+                          void *d_out, uint64_t out_cap, void *stream) {
+  uint64_t lo = 0, hi = 0;
+  int rc = aceapex_region_lookup(a, chrom, pos, len, line_width, &lo, &hi);
+  if (rc) return rc;
+  if (!d_out) return ACEAPEX_EINVAL;
+  if (out_cap < len) return ACEAPEX_ERANGE;
+  if (cudaSetDevice(a->device) != cudaSuccess) return ACEAPEX_ECUDA;
+  if ((rc = ensure_scratch(a))) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  OutView v;
+  uint32_t n = 0;
+  rc = decode_closure(a, lo >> a->h.log2_S, (hi - 1) >> a->h.log2_S, st, &v, &n, true);
+  if (rc) return rc;
+  cudaError_t e = launch_gather_bases(v, a->h.log2_S, lo, (uint32_t)(pos % line_width), line_width, len,
+                                      static_cast<uint8_t *>(d_out), st);
+  if (e == cudaSuccess) e = launch_clear_pages(a->d_page.p, a->d_work.p, n, st);
+  return cuda_status(e);
+}
+
 int aceapex_last_error(aceapex_archive *a, int sync, void *stream) {
   if (!a) return ACEAPEX_EINVAL;
   if (cudaSetDevice(a->device) != cudaSuccess) return ACEAPEX_ECUDA;
@@ -643,6 +688,11 @@ int aceapex_encode(const void *h_in, uint64_t n, uint32_t log2_B, uint32_t min_m
 }
 
 void aceapex_free(void *p) { std::free(p); }
+
+uint64_t aceapex_fasta_index(const void *h_in, uint64_t n, uint64_t *h_out, uint64_t cap, uint32_t *line_width) {
+  if (!h_in) return 0;
+  return fasta_index(static_cast<const uint8_t *>(h_in), n, h_out, cap, line_width);
+}
 
 uint64_t aceapex_fastq_index(const void *h_in, uint64_t n, uint64_t *h_out, uint64_t cap) {
   if (!h_in) return 0;

@@ -610,6 +610,17 @@ __global__ void gather_kernel(OutView v, uint32_t log2_S, uint64_t lo, uint64_t 
   }
 }
 
+// bases [0, n) of a FASTA region whose first base sits at lo with line phase
+// `phase` (its position within a line of L bases): base i is at
+// lo + i + (phase + i) / L, the newline after every L bases skipped
+__global__ void gather_bases_kernel(OutView v, uint32_t log2_S, uint64_t lo, uint32_t phase, uint32_t L, uint64_t n,
+                                    uint8_t *dst) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint8_t *p = at(v, lo + i + (phase + i) / L, log2_S);
+    dst[i] = p ? *p : 0;
+  }
+}
+
 constexpr uint64_t kGatherChunk = 65536;
 
 __global__ void multi_gather_kernel(const GatherJob *jobs, uint32_t n_jobs, uint64_t n_chunks) {
@@ -834,6 +845,14 @@ cudaError_t launch_gather(OutView v, uint32_t log2_S, uint64_t lo, uint64_t hi, 
   uint64_t n = hi - lo;
   int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   gather_kernel<<<grid, 256, 0, st>>>(v, log2_S, lo, n, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_bases(OutView v, uint32_t log2_S, uint64_t lo, uint32_t phase, uint32_t line_width,
+                                uint64_t n, uint8_t *dst, cudaStream_t st) {
+  if (!n) return cudaSuccess;
+  int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  gather_bases_kernel<<<grid, 256, 0, st>>>(v, log2_S, lo, phase, line_width, n, dst);
   return cudaGetLastError();
 }
 

@@ -94,6 +94,11 @@ int decode_grid(int device, int block);
 // Gather [lo, hi) through a view into a flat buffer.
 cudaError_t launch_gather(OutView v, uint32_t log2_S, uint64_t lo, uint64_t hi, uint8_t *dst, cudaStream_t st);
 
+// n FASTA bases from lo (line phase `phase`, lines of line_width bases each
+// followed by a newline) into a flat buffer, newlines dropped
+cudaError_t launch_gather_bases(OutView v, uint32_t log2_S, uint64_t lo, uint32_t phase, uint32_t line_width,
+                                uint64_t n, uint8_t *dst, cudaStream_t st);
+
 // page[work[i].seg] = i for i < n (paged views)
 cudaError_t launch_set_pages(uint32_t *page, const WorkItem *work, uint32_t n, cudaStream_t st);
 

@@ -181,6 +181,41 @@ def test_read_lookup_then_decode():
             arc.read_lookup(2000)
 
 
+def test_decode_region_by_coordinates():
+    """chr:pos lookups through the coordinate index: the bases of (record,
+    position, length) equal the record's sequence with its newlines removed,
+    across line ends, segment ends and record ends."""
+    f = synth.fasta(3_000_000, seed=13, n_chrom=3)
+    idx, width = ace.fasta_index(f)
+    a = ace.encode(f, min_match=12, dist_bound=1 << 20, reads=idx)
+    text = f.tobytes()
+    seqs = []
+    for k in range(len(idx) // 2):
+        end = int(idx[2 * k + 2]) if 2 * k + 2 < len(idx) else len(text)
+        seqs.append(text[int(idx[2 * k + 1]):end].replace(b"\n", b""))
+    rng = np.random.default_rng(4)
+    with ace.Archive(a) as arc:
+        cases = [(0, 0, 1), (0, 0, 60), (0, 59, 2), (1, 0, 12345), (2, len(seqs[2]) - 1, 1),
+                 (1, len(seqs[1]) - 150, 150)]
+        for _ in range(40):
+            k = int(rng.integers(0, len(seqs)))
+            n = int(rng.integers(1, 20_000))
+            p = int(rng.integers(0, len(seqs[k]) - n))
+            cases.append((k, p, n))
+        for k, p, n in cases:
+            lo, hi = arc.region_lookup(k, p, n, width)
+            raw = text[lo:hi]
+            assert raw.replace(b"\n", b"") == seqs[k][p:p + n]
+            out = torch.zeros(n, dtype=torch.uint8, device="cuda")
+            arc.decode_region(k, p, n, out, width)
+            arc.check()
+            assert out.cpu().numpy().tobytes() == seqs[k][p:p + n], (k, p, n)
+        for bad in [(3, 0, 1), (0, len(seqs[0]), 1), (0, len(seqs[0]) - 5, 6)]:
+            with pytest.raises(ace.AceapexError) as e:
+                arc.region_lookup(*bad, width)
+            assert e.value.code == ace.ERANGE
+
+
 def test_level_counts_match_directory():
     d = synth.pe_fastq(2 << 20, ref_len=500_000)
     a = ace.encode(d, min_match=12, max_level=5)

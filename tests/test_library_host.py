@@ -96,6 +96,23 @@ def test_library_encoder_deterministic_across_threads():
     assert np.array_equal(a1, a8)
 
 
+def test_fasta_coordinate_index():
+    """Record and sequence starts of every FASTA record, and the line width,
+    against a plain scan of the lines."""
+    f = synth.fasta(1_500_000, seed=9, n_chrom=5)
+    idx, width = ace.fasta_index(f)
+    text = f.tobytes()
+    want, pos = [], 0
+    for line in text.split(b"\n")[:-1]:
+        if line.startswith(b">"):
+            want += [pos, pos + len(line) + 1]
+        pos += len(line) + 1
+    if not text.endswith(b"\n"):
+        want.append(len(text) - 1)  # marks an unterminated last line
+    assert idx.tolist() == want and len(want) in (10, 11)
+    assert width == 60
+
+
 def test_empty_input():
     a = ace.encode(np.zeros(0, np.uint8))
     assert oracle.decode(a).size == 0
