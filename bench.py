@@ -176,15 +176,24 @@ def base_line(args, value, ms_per_step, world, config, **extra):
 
 
 def cpu_oracle_baseline(arc, data, what):
-    """The CPU oracle decoder as it stands (single thread) on the given archive."""
+    """The CPU oracle decoder as it stands (single thread) on the given archive,
+    and, beside it, the oracle's segment decoder run level by level on every
+    host core (the all-core baseline)."""
     import oracle
 
     t = time.perf_counter()
     out = oracle.decode(arc)
     dt = time.perf_counter() - t
+    cores = len(os.sched_getaffinity(0))
+    t = time.perf_counter()
+    out2 = oracle.decode_wavefront(arc, cores)
+    dt2 = time.perf_counter() - t
     return {"value": data.size / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{what}: one sequential pass over {data.size} bytes ({dt:.1f} s); host has "
-                      f"{len(os.sched_getaffinity(0))} cores", "bit_exact": bool(np.array_equal(out, data))}
+            "sample": f"{what}: one sequential pass over {data.size} bytes ({dt:.1f} s); host has {cores} cores",
+            "bit_exact": bool(np.array_equal(out, data)),
+            "all_cores": {"value": data.size / dt2 / 1e9, "unit": "GB/s", "cores": cores,
+                          "kind": "oracle segment decoder, level-by-level wavefront on all host cores",
+                          "bit_exact": bool(np.array_equal(out2, data))}}
 
 
 # ------------------------------------------------------------------- fastq

@@ -59,7 +59,7 @@ def build(force: bool = False) -> str:
     """Compile liboracle.so (plain C, portable flags)."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC])
         os.replace(tmp, _SO)
     return _SO
 
@@ -89,6 +89,8 @@ def _load():
             lib.orc_free.argtypes = [ctypes.c_void_p]
             lib.orc_decode.argtypes = [u8p, ctypes.c_uint64, u8p, ctypes.c_uint64]
             lib.orc_decode.restype = ctypes.c_int
+            lib.orc_decode_wavefront.argtypes = [u8p, ctypes.c_uint64, u8p, ctypes.c_uint64, ctypes.c_int]
+            lib.orc_decode_wavefront.restype = ctypes.c_int
             lib.orc_decode_stream.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                               ctypes.c_uint64, u32p, ctypes.c_uint64]
             lib.orc_decode_stream.restype = ctypes.c_int
@@ -204,6 +206,18 @@ def decode(arc) -> np.ndarray:
     if rc:
         raise OracleError(rc, "orc_decode")
     return out
+
+
+def decode_wavefront(arc, threads: int) -> np.ndarray:
+    """The segment decoder run level by level on `threads` host threads."""
+    lib = _load()
+    a = _buf(arc)
+    n = info(a)["n"]
+    out = np.zeros(max(n, 1), dtype=np.uint8)
+    rc = lib.orc_decode_wavefront(_p8(a), a.size, _p8(out), out.size, threads)
+    if rc:
+        raise OracleError(rc, "orc_decode_wavefront")
+    return out[:n]
 
 
 def decode_stream_crcs(arc, lo: int, hi: int, window: int) -> np.ndarray:

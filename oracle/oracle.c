@@ -27,10 +27,15 @@
  *   orc_segment_info     per-segment commands, symbols and final states for
  *                        the invariant tests.
  *   orc_fastq_record_starts  the read-to-block index of paper §4.1.
+ *   orc_decode_wavefront the same segment decoder run level by level on
+ *                        several host threads (all segments of a level at
+ *                        once, a barrier between levels): the all-core CPU
+ *                        baseline, the analog of the paper's CPU-T8 runs.
  *
  * Everything is integer arithmetic; there is no precision axis (the paper
  * requires bit-perfect output, §2.2).
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -891,4 +896,74 @@ uint64_t orc_fastq_record_starts(const uint8_t *in, uint64_t n, uint64_t *out, u
     if (in[p] == '\n') { ++line; at_line_start = 1; }
   }
   return k;
+}
+
+/* ---------------------------------------------- all-core CPU baseline */
+
+typedef struct {
+  const arc_t *A;
+  uint8_t *out;
+  const uint64_t *segs; /* the segments of the current level */
+  uint64_t n;
+  uint64_t next;        /* next index into segs (taken under mu) */
+  int rc;
+  pthread_mutex_t mu;
+} wave_t;
+
+static void *wave_worker(void *arg) {
+  wave_t *W = (wave_t *)arg;
+  scratch_t w;
+  int rc = scratch_new(&w, W->A->g.n_seg);
+  for (;;) {
+    pthread_mutex_lock(&W->mu);
+    if (rc && !W->rc) W->rc = rc;
+    const uint64_t i = W->rc ? W->n : W->next++;
+    pthread_mutex_unlock(&W->mu);
+    if (i >= W->n) break;
+    rc = decode_segment(W->A, W->segs[i], W->out, ~(uint64_t)0, w.sym, w.cmds, w.mark, w.tmp);
+  }
+  scratch_free(&w);
+  return NULL;
+}
+
+/*
+ * Decode into out[0..N) on `threads` host threads: every segment of level L
+ * reads only segments of lower levels, so the segments of one level decode
+ * in any order once the lower levels are done. Returns an ORC_* status.
+ */
+int orc_decode_wavefront(const uint8_t *a, uint64_t len, uint8_t *out, uint64_t cap, int threads) {
+  arc_t A;
+  int rc = arc_open(a, len, &A);
+  if (rc) { arc_release(&A); return rc; }
+  if (cap < A.g.n) { arc_release(&A); return ORC_ERANGE; }
+  if (threads < 1) threads = 1;
+  uint64_t *segs = (uint64_t *)malloc(sizeof(uint64_t) * (A.g.n_seg + 1));
+  pthread_t *tid = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)threads);
+  if (!segs || !tid) { free(segs); free(tid); arc_release(&A); return ORC_ENOMEM; }
+  uint32_t max_level = 0;
+  for (uint64_t s = 0; s < A.g.n_seg; ++s) {
+    uint32_t l = get_u16(A.a + A.off_dir + 24 * s + 20);
+    if (l > max_level) max_level = l;
+  }
+  wave_t W;
+  W.A = &A;
+  W.out = out;
+  W.segs = segs;
+  W.rc = ORC_OK;
+  pthread_mutex_init(&W.mu, NULL);
+  for (uint32_t L = 0; L <= max_level && W.rc == ORC_OK; ++L) {
+    uint64_t n = 0;
+    for (uint64_t s = 0; s < A.g.n_seg; ++s)
+      if (get_u16(A.a + A.off_dir + 24 * s + 20) == L) segs[n++] = s;
+    W.n = n;
+    W.next = 0;
+    for (int t = 0; t < threads; ++t) pthread_create(&tid[t], NULL, wave_worker, &W);
+    for (int t = 0; t < threads; ++t) pthread_join(tid[t], NULL);
+  }
+  rc = W.rc;
+  pthread_mutex_destroy(&W.mu);
+  free(segs);
+  free(tid);
+  arc_release(&A);
+  return rc;
 }

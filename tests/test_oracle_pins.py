@@ -320,3 +320,15 @@ def test_stream_crcs_equal_zlib(D):
         crcs = oracle.decode_stream_crcs(a, lo, hi, w)
         ref = [zlib.crc32(data[b:min(hi, b + w)].tobytes()) for b in range(lo, hi, w)]
         assert list(crcs) == ref
+
+
+def test_wavefront_decoder_equals_sequential():
+    """The all-core baseline (the oracle's segment decoder run level by level
+    on several threads) gives the sequential decoder's bytes, for many levels
+    and for intra-segment chains."""
+    import paper_2606_18900_gb300 as ace
+    cases = [synth.pe_fastq(2 << 20, ref_len=300_000), synth.random_bytes(14, 2, 30_000, b"ab")]
+    for d, kw in ((cases[0], dict(min_match=12)), (cases[1], dict(log2_B=6, min_match=2))):
+        a = ace.encode(d, **kw)
+        for t in (1, 3, 8):
+            assert np.array_equal(oracle.decode_wavefront(a, t), d)
