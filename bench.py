@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="fastq", choices=["fastq", "tiny", "batch", "genome", "serve", "entropy"])
+    p.add_argument("--workload", default="fastq", choices=["fastq", "tiny", "batch", "genome", "serve", "entropy", "fastq_streams"])
     p.add_argument("--log2-block", type=int, default=14)
     p.add_argument("--size", type=int, default=0, help="workload bytes (0 = the workload's default)")
     p.add_argument("--min-match", type=int, default=0, help="0 = the workload's default")
@@ -468,6 +468,58 @@ def workload_entropy(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ fastq streams
+
+def workload_fastq_streams(args):
+    """The paired-end FASTQ stored as four archives of its line streams
+    (headers, sequences, '+' lines, qualities): ratio against the single
+    archive, and the whole-file decode (a persistent launch per part, device
+    newline index, record interleave)."""
+    import torch
+
+    import paper_2606_18900_gb300 as ace
+    import synth
+
+    size = args.size or (1 << 30)
+    data = synth.pe_fastq(size)
+    N = data.size
+    t = time.perf_counter()
+    streams, n_rec = ace.fastq_split(data)
+    split_s = time.perf_counter() - t
+    t = time.perf_counter()
+    arcs = [ace.encode(x, min_match=args.min_match or 16) for x in streams]
+    enc_s = time.perf_counter() - t
+    single = ace.encode(data, min_match=args.min_match or 16)
+    parts = [ace.Archive(a) for a in arcs]
+    out = torch.empty(N, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    run = lambda: ace.decode_fastq_streams(parts, out, stream)
+    for _ in range(args.warmup):
+        run()
+    for p_ in parts:
+        p_.check(stream)
+    ok = bool(np.array_equal(out.cpu().numpy(), data))
+    if not ok:
+        raise SystemExit("bench: reassembled FASTQ differs from the input")
+    step_ms = timed_steps(run, stream, args.steps)
+    for p_ in parts:
+        p_.check(stream)
+    total_ms = float(sum(step_ms))
+    comp = sum(int(a.size) for a in arcs)
+    line = base_line(args, N * args.steps / (total_ms * 1e-3) / 1e9, total_ms / args.steps, 1,
+                     {"workload": f"paired-end FASTQ {N} bytes as four line-stream archives, whole-file decode",
+                      "records": n_rec, "stream_bytes": [int(x.size) for x in streams],
+                      "archive_bytes": [int(a.size) for a in arcs],
+                      "ratio_streams": round(N / comp, 3), "ratio_single_archive": round(N / single.size, 3),
+                      "ratio_gain_pct": round(100 * (single.size / comp - 1), 1),
+                      "split_seconds": round(split_s, 2), "encode_seconds": round(enc_s, 2),
+                      "l2": "inputs larger than L2"},
+                     gpu_launches=args.steps * (2 * 4 + 3 * 4 + 1), bit_exact=ok, ms_median=float(np.median(step_ms)))
+    print(json.dumps(line), flush=True)
+    for p_ in parts:
+        p_.close()
+
+
 # ------------------------------------------------------------------- batch
 
 def workload_batch(args):
@@ -787,6 +839,8 @@ def main():
         workload_serve(args)
     elif args.workload == "entropy":
         workload_entropy(args)
+    elif args.workload == "fastq_streams":
+        workload_fastq_streams(args)
     else:
         workload_genome(args)
 

@@ -300,6 +300,27 @@ int aceapex_region_lookup(const aceapex_archive *a, uint64_t chrom, uint64_t pos
 int aceapex_decode_region(aceapex_archive *a, uint64_t chrom, uint64_t pos, uint64_t len, uint32_t line_width,
                           void *d_out, uint64_t out_cap, void *stream);
 
+/*
+ * FASTQ stream separation (the paper's ids / sequences / qualities split,
+ * reported there for +10-11 % ratio): line k of h_in goes to stream k mod 4
+ * (headers, sequences, '+' lines, qualities), each line with its newline. The
+ * four streams are written back to back to h_out (n bytes, caller-owned) and
+ * their lengths to h_lens[0..3]. Returns the number of records. Host only.
+ */
+uint64_t aceapex_fastq_split(const void *h_in, uint64_t n, void *h_out, uint64_t *h_lens);
+
+/*
+ * Whole-file decode of a FASTQ stored as four archives of its line streams
+ * (parts[k] holds stream k of aceapex_fastq_split): each part decodes with
+ * its own persistent launch into scratch owned by parts[0], a newline index
+ * of each stream is built on the device, and one warp per record copies its
+ * four lines to d_out[0 .. N), N the sum of the streams' sizes. Stream-
+ * ordered; decode errors are latched in each part's error word, and a
+ * stream that is not made of FASTQ lines in parts[0]'s. Each stream must be below 4 GiB. Errors:
+ * EINVAL, ERANGE (out_cap < N or a stream too large), ENOMEM, ECUDA.
+ */
+int aceapex_decode_fastq_streams(aceapex_archive *const *parts, void *d_out, uint64_t out_cap, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -142,6 +142,9 @@ def lib():
             L.aceapex_free.restype = None
             L.aceapex_fastq_index.argtypes = [vp, u64, u64p, u64]
             L.aceapex_fastq_index.restype = u64
+            L.aceapex_fastq_split.argtypes = [vp, u64, vp, u64p]
+            L.aceapex_fastq_split.restype = u64
+            L.aceapex_decode_fastq_streams.argtypes = [ctypes.POINTER(vp), vp, u64, vp]
             L.aceapex_fasta_index.argtypes = [vp, u64, u64p, u64, ctypes.POINTER(ctypes.c_uint32)]
             L.aceapex_fasta_index.restype = u64
             L.aceapex_region_lookup.argtypes = [vp, u64, u64, u64, ctypes.c_uint32, u64p, u64p]
@@ -214,6 +217,25 @@ def fastq_index(data) -> np.ndarray:
     out = np.zeros(max(n, 1), dtype=np.uint64)
     L.aceapex_fastq_index(buf.ctypes.data, buf.size, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), n)
     return out[:n]
+
+
+def fastq_split(data):
+    """The four line streams of a FASTQ (headers, sequences, '+' lines,
+    qualities) and its record count."""
+    L = lib()
+    buf = _as_u8(data)
+    out = np.empty(max(buf.size, 1), dtype=np.uint8)
+    lens = (ctypes.c_uint64 * 4)()
+    n = L.aceapex_fastq_split(buf.ctypes.data, buf.size, out.ctypes.data, lens)
+    cuts = np.cumsum([0] + [int(x) for x in lens])
+    return [out[cuts[k]:cuts[k + 1]] for k in range(4)], int(n)
+
+
+def decode_fastq_streams(parts, out, stream=None):
+    """Reassemble a FASTQ from the Archives of its four line streams into out."""
+    hs = (ctypes.c_void_p * 4)(*[p._h for p in parts])
+    _check(lib().aceapex_decode_fastq_streams(hs, _ptr(out), out.numel() * out.element_size(), _stream(stream)),
+           "aceapex_decode_fastq_streams")
 
 
 def fasta_index(data):

@@ -126,6 +126,10 @@ struct aceapex_archive {
   DBuf<DevArchive> d_batch_arcs;
   DBuf<OutView> d_batch_views;
   Staging stage_batch;
+  // FASTQ stream reassembly (when this handle is a set's first part)
+  DBuf<uint8_t> d_fq_streams;
+  DBuf<uint32_t> d_fq_counts, d_fq_nl;
+  DBuf<uint64_t> d_fq_offs;
 
   uint32_t *err() const { return d_words.p; }
   uint32_t *epoch() const { return d_words.p + 1; }
@@ -152,6 +156,7 @@ struct aceapex_archive {
     d_payload.release(); d_dir.release(); d_lut.release(); d_flags.release(); d_order.release();
     d_words.release(); d_blocked.release(); d_scratch.release(); d_page.release(); d_arena.release();
     d_work.release(); d_ring.release(); d_seg_crc.release(); d_batch_arcs.release(); d_batch_views.release();
+    d_fq_streams.release(); d_fq_counts.release(); d_fq_nl.release(); d_fq_offs.release();
     stage_work.release();
     stage_batch.release();
   }

@@ -638,4 +638,31 @@ uint64_t fasta_index(const uint8_t *in, uint64_t n, uint64_t *out, uint64_t cap,
   return k;
 }
 
+// FASTQ stream separation: line k of the input goes to stream k mod 4
+// (headers, sequences, '+' lines, qualities), each line with its newline; the
+// streams are written back to back to out (n bytes) and their lengths to
+// len[0..3]. Returns the number of records (lines of stream 0).
+uint64_t fastq_split(const uint8_t *in, uint64_t n, uint8_t *out, uint64_t len[4]) {
+  for (int k = 0; k < 4; ++k) len[k] = 0;
+  uint64_t line = 0;
+  for (uint64_t p = 0; p < n;) {  // pass 1: stream lengths
+    const void *e = std::memchr(in + p, '\n', n - p);
+    const uint64_t q = e ? static_cast<const uint8_t *>(e) - in + 1 : n;
+    len[line & 3] += q - p;
+    ++line;
+    p = q;
+  }
+  uint64_t at[4] = {0, len[0], len[0] + len[1], len[0] + len[1] + len[2]};
+  line = 0;
+  for (uint64_t p = 0; p < n;) {  // pass 2: copy
+    const void *e = std::memchr(in + p, '\n', n - p);
+    const uint64_t q = e ? static_cast<const uint8_t *>(e) - in + 1 : n;
+    std::memcpy(out + at[line & 3], in + p, q - p);
+    at[line & 3] += q - p;
+    ++line;
+    p = q;
+  }
+  return (line + 3) / 4;
+}
+
 }  // namespace aceapex

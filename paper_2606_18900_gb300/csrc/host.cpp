@@ -19,6 +19,7 @@ int encode_archive(const uint8_t *in, uint64_t n, uint32_t log2_B, uint32_t min_
                    const uint64_t *reads, uint64_t n_reads, int threads, uint8_t **out, uint64_t *out_len);
 uint64_t fastq_index(const uint8_t *in, uint64_t n, uint64_t *out, uint64_t cap);
 uint64_t fasta_index(const uint8_t *in, uint64_t n, uint64_t *out, uint64_t cap, uint32_t *line_width);
+uint64_t fastq_split(const uint8_t *in, uint64_t n, uint8_t *out, uint64_t len[4]);
 }  // namespace aceapex
 
 using namespace aceapex;
@@ -688,6 +689,60 @@ int aceapex_encode(const void *h_in, uint64_t n, uint32_t log2_B, uint32_t min_m
 }
 
 void aceapex_free(void *p) { std::free(p); }
+
+uint64_t aceapex_fastq_split(const void *h_in, uint64_t n, void *h_out, uint64_t *h_lens) {
+  if (!h_in || !h_out || !h_lens) return 0;
+  return fastq_split(static_cast<const uint8_t *>(h_in), n, static_cast<uint8_t *>(h_out), h_lens);
+}
+
+int aceapex_decode_fastq_streams(aceapex_archive *const *parts, void *d_out, uint64_t out_cap, void *stream) {
+  if (!parts) return ACEAPEX_EINVAL;
+  for (int k = 0; k < 4; ++k)
+    if (!parts[k] || parts[k]->device != parts[0]->device) return ACEAPEX_EINVAL;
+  aceapex_archive *A = parts[0];
+  uint64_t len[4], N = 0, chunks_max = 0, offs_n = 0, cap[4], nl_n = 0;
+  for (int k = 0; k < 4; ++k) {
+    len[k] = parts[k]->h.n;
+    if (len[k] >= (uint64_t(1) << 32)) return ACEAPEX_ERANGE;  // u32 newline positions
+    N += len[k];
+    const uint64_t chunks = (len[k] + 65535) / 65536;
+    chunks_max = std::max(chunks_max, chunks);
+    offs_n += chunks + 1;
+    cap[k] = len[k] / 2 + 1;  // FASTQ lines are at least 2 bytes long
+    nl_n += cap[k];
+  }
+  if (!d_out && N) return ACEAPEX_EINVAL;
+  if (out_cap < N) return ACEAPEX_ERANGE;
+  if (N == 0) return ACEAPEX_OK;
+  if (cudaSetDevice(A->device) != cudaSuccess) return ACEAPEX_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (A->d_fq_streams.n < N || A->d_fq_counts.n < chunks_max || A->d_fq_offs.n < offs_n || A->d_fq_nl.n < nl_n) {
+    cudaStreamSynchronize(st);
+    if (A->d_fq_streams.alloc(N) != cudaSuccess || A->d_fq_counts.alloc(std::max<uint64_t>(chunks_max, 1)) != cudaSuccess ||
+        A->d_fq_offs.alloc(offs_n) != cudaSuccess || A->d_fq_nl.alloc(nl_n) != cudaSuccess)
+      return ACEAPEX_ENOMEM;
+  }
+  void *outs[4];
+  const uint8_t *base[4];
+  uint32_t *nl[4];
+  uint64_t at = 0, nat = 0;
+  for (int k = 0; k < 4; ++k) {
+    outs[k] = A->d_fq_streams.p + at;
+    base[k] = A->d_fq_streams.p + at;
+    nl[k] = A->d_fq_nl.p + nat;
+    at += len[k];
+    nat += cap[k];
+  }
+  // each part fills the whole GPU with its own persistent launch (a batch
+  // launch would give each of the four archives a single CTA)
+  for (int k = 0; k < 4; ++k) {
+    if (!len[k]) continue;
+    int rc = aceapex_decode_all(parts[k], outs[k], len[k], stream, nullptr);
+    if (rc) return rc;
+  }
+  return cuda_status(launch_fastq_interleave(base, len, A->d_fq_counts.p, A->d_fq_offs.p, nl, cap, A->err(),
+                                             static_cast<uint8_t *>(d_out), st));
+}
 
 uint64_t aceapex_fasta_index(const void *h_in, uint64_t n, uint64_t *h_out, uint64_t cap, uint32_t *line_width) {
   if (!h_in) return 0;

@@ -780,6 +780,121 @@ __global__ void __launch_bounds__(1024) window_crc_kernel(const uint32_t *seg_cr
   if (threadIdx.x == 0) out[k] = part[0] ^ crc_shift(gops, 0xFFFFFFFFu, plen[0]) ^ 0xFFFFFFFFu;
 }
 
+
+// ------------------------------------------------- FASTQ stream separation
+// A FASTQ split into its four line streams (headers, sequences, '+' lines,
+// qualities) is put back together on the device: the newlines of each
+// decoded stream are indexed (count per chunk, scan, positions), then one warp
+// per record copies line r of every stream to its place. Record r starts at
+// the sum over the streams of the start of their line r, since every earlier
+// line of every stream precedes it in the FASTQ.
+constexpr uint32_t kNlChunk = 65536;
+
+// counts[c] = newlines in chunk c of buf[0, n); one CTA of 256 threads per chunk
+__global__ void nl_count_kernel(const uint8_t *buf, uint64_t n, uint32_t *counts) {
+  const uint64_t c0 = (uint64_t)blockIdx.x * kNlChunk, c1 = c0 + kNlChunk < n ? c0 + kNlChunk : n;
+  uint32_t k = 0;
+  for (uint64_t p = c0 + threadIdx.x; p < c1; p += blockDim.x) k += buf[p] == '\n';
+  for (int d = 16; d; d >>= 1) k += __shfl_xor_sync(kFull, k, d);
+  __shared__ uint32_t part[8];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = k;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < 8; ++w) t += part[w];
+    counts[blockIdx.x] = t;
+  }
+}
+
+// offs[c] = newlines before chunk c; offs[n_chunks] = total (one CTA)
+__global__ void nl_scan_kernel(const uint32_t *counts, uint32_t n_chunks, uint64_t *offs) {
+  __shared__ uint64_t part[1024];
+  const uint32_t per = (n_chunks + blockDim.x - 1) / blockDim.x;
+  const uint32_t i0 = threadIdx.x * per, i1 = i0 + per < n_chunks ? i0 + per : n_chunks;
+  uint64_t t = 0;
+  for (uint32_t i = i0; i < i1; ++i) t += counts[i];
+  part[threadIdx.x] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t run = 0;
+    for (uint32_t w = 0; w < blockDim.x; ++w) {
+      const uint64_t v = part[w];
+      part[w] = run;
+      run += v;
+    }
+    offs[n_chunks] = run;
+  }
+  __syncthreads();
+  uint64_t run = part[threadIdx.x];
+  for (uint32_t i = i0; i < i1; ++i) {
+    offs[i] = run;
+    run += counts[i];
+  }
+}
+
+// nl[j] = position of the j-th newline of buf (j < cap; err set beyond)
+__global__ void nl_positions_kernel(const uint8_t *buf, uint64_t n, const uint64_t *offs, uint32_t *nl, uint64_t cap,
+                                    uint32_t *err) {
+  const uint64_t c0 = (uint64_t)blockIdx.x * kNlChunk, c1 = c0 + kNlChunk < n ? c0 + kNlChunk : n;
+  // each warp takes 32-byte windows in order; a ballot places the window's
+  // newlines after those of the earlier windows of the chunk
+  __shared__ uint32_t wcount[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint64_t span = (c1 - c0 + 7) / 8, w0 = c0 + wid * span, w1 = w0 + span < c1 ? w0 + span : c1;
+  uint32_t mine = 0;
+  for (uint64_t p = w0 + lane; p < w1 + lane; p += 32) mine += (p < w1 && buf[p] == '\n');
+  for (int d = 16; d; d >>= 1) mine += __shfl_xor_sync(kFull, mine, d);
+  if (lane == 0) wcount[wid] = mine;
+  __syncthreads();
+  uint64_t base = offs[blockIdx.x];
+  for (int w = 0; w < wid; ++w) base += wcount[w];
+  for (uint64_t p = w0; p < w1; p += 32) {
+    const bool is_nl = p + lane < w1 && buf[p + lane] == '\n';
+    const uint32_t m = __ballot_sync(kFull, is_nl);
+    if (is_nl) {
+      const uint64_t j = base + __popc(m & ((1u << lane) - 1u));
+      if (j < cap) nl[j] = (uint32_t)(p + lane);
+      else latch(err, kErrCorrupt);
+    }
+    base += __popc(m);
+  }
+}
+
+struct LineStreams {
+  const uint8_t *base[4];
+  const uint32_t *nl[4];
+  const uint64_t *count[4];  // device: newlines of each stream
+  uint64_t len[4];
+};
+
+// one warp per record (grid-stride): line r of stream k is [s, e) with
+// s = nl_k[r - 1] + 1 (0 for r = 0) and e = nl_k[r] + 1, or the stream end
+// for a last line without newline
+__global__ void interleave_kernel(LineStreams S, uint8_t *out) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  uint64_t cnt[4], R = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) cnt[k] = *S.count[k];
+  R = cnt[0] + (S.len[0] && (cnt[0] == 0 || S.nl[0][cnt[0] - 1] != S.len[0] - 1) ? 1 : 0);
+  for (uint64_t r = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < R; r += warps) {
+    uint64_t s[4], e[4], o = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      s[k] = r == 0 ? 0 : (r - 1 < cnt[k] ? (uint64_t)S.nl[k][r - 1] + 1 : S.len[k]);
+      e[k] = r < cnt[k] ? (uint64_t)S.nl[k][r] + 1 : S.len[k];
+      if (e[k] < s[k]) e[k] = s[k];
+      o += s[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint8_t *src = S.base[k] + s[k];
+      const uint64_t len = e[k] - s[k];
+      for (uint64_t i = lane; i < len; i += 32) out[o + i] = src[i];
+      o += len;
+    }
+  }
+}
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
@@ -853,6 +968,34 @@ cudaError_t launch_gather_bases(OutView v, uint32_t log2_S, uint64_t lo, uint32_
   if (!n) return cudaSuccess;
   int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   gather_bases_kernel<<<grid, 256, 0, st>>>(v, log2_S, lo, phase, line_width, n, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fastq_interleave(const uint8_t *const base[4], const uint64_t len[4], uint32_t *counts,
+                                    uint64_t *offs, uint32_t *const nl[4], const uint64_t cap[4], uint32_t *err,
+                                    uint8_t *out, cudaStream_t st) {
+  LineStreams S{};
+  uint64_t off_at = 0;
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t chunks = (uint32_t)((len[k] + kNlChunk - 1) / kNlChunk);
+    uint64_t *o = offs + off_at;
+    if (chunks) {
+      nl_count_kernel<<<chunks, 256, 0, st>>>(base[k], len[k], counts);
+      nl_scan_kernel<<<1, 1024, 0, st>>>(counts, chunks, o);
+      nl_positions_kernel<<<chunks, 256, 0, st>>>(base[k], len[k], o, nl[k], cap[k], err);
+    } else if (cudaMemsetAsync(o, 0, sizeof(uint64_t), st) != cudaSuccess) {
+      return cudaGetLastError();
+    }
+    S.base[k] = base[k];
+    S.nl[k] = nl[k];
+    S.count[k] = o + chunks;
+    S.len[k] = len[k];
+    off_at += chunks + 1;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  interleave_kernel<<<8 * sms, 256, 0, st>>>(S, out);
   return cudaGetLastError();
 }
 

@@ -114,6 +114,15 @@ struct GatherJob {
 // All jobs in one launch: the jobs' 64 KiB chunks are spread over the CTAs.
 cudaError_t launch_multi_gather(const GatherJob *jobs, uint32_t n_jobs, uint64_t n_chunks, cudaStream_t st);
 
+// Reassembles a FASTQ from its four decoded line streams (base[k], len[k]
+// bytes): newline index of each stream (counts: one u32 per 64 KiB chunk of
+// the longest stream; offs: chunks + 1 u64 per stream; nl[k]: cap[k] u32
+// positions, err latched beyond), then one warp per record copies its four
+// lines to out.
+cudaError_t launch_fastq_interleave(const uint8_t *const base[4], const uint64_t len[4], uint32_t *counts,
+                                    uint64_t *offs, uint32_t *const nl[4], const uint64_t cap[4], uint32_t *err,
+                                    uint8_t *out, cudaStream_t st);
+
 // CRC-32 of each window [lo + k*window, ...) of the ring view, written to crc[k].
 cudaError_t launch_window_crc(OutView v, uint64_t lo, uint64_t hi, uint64_t window, uint32_t *crc, uint32_t *seg_crc,
                               uint32_t log2_S, cudaStream_t st);

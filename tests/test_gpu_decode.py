@@ -216,6 +216,24 @@ def test_decode_region_by_coordinates():
             assert e.value.code == ace.ERANGE
 
 
+@pytest.mark.parametrize("cut", [0, 1, 77])
+def test_fastq_stream_separation_round_trip(cut):
+    """A FASTQ stored as four archives of its line streams decodes (a launch
+    per part, a device newline index per stream, one warp per record) back to
+    the original bytes, also when the file ends inside a record."""
+    d = synth.pe_fastq(6 << 20, ref_len=1_000_000)
+    d = d[: d.size - cut]
+    streams, n_rec = ace.fastq_split(d)
+    parts = [ace.Archive(ace.encode(x, min_match=16)) for x in streams]
+    out = torch.zeros(d.size, dtype=torch.uint8, device="cuda")
+    ace.decode_fastq_streams(parts, out)
+    for p in parts:
+        p.check()
+    assert_same(out.cpu().numpy(), d)
+    for p in parts:
+        p.close()
+
+
 def test_level_counts_match_directory():
     d = synth.pe_fastq(2 << 20, ref_len=500_000)
     a = ace.encode(d, min_match=12, max_level=5)

@@ -113,6 +113,25 @@ def test_fasta_coordinate_index():
     assert width == 60
 
 
+def test_fastq_split_streams():
+    """Line k of the FASTQ lands in stream k mod 4, in order; the streams hold
+    every byte once; a FASTQ cut inside a record splits the same way."""
+    d = synth.tiny_fastq()
+    for cut in (d.size, d.size - 1, d.size - 200):
+        x = d[:cut]
+        streams, n_rec = ace.fastq_split(x)
+        lines = x.tobytes().split(b"\n")
+        if lines[-1] == b"":
+            lines = lines[:-1]
+            ends = [b"\n"] * len(lines)
+        else:
+            ends = [b"\n"] * (len(lines) - 1) + [b""]
+        want = [b"".join(l + e for i, (l, e) in enumerate(zip(lines, ends)) if i % 4 == k) for k in range(4)]
+        assert [s.tobytes() for s in streams] == want
+        assert n_rec == (len(lines) + 3) // 4
+        assert sum(s.size for s in streams) == x.size
+
+
 def test_empty_input():
     a = ace.encode(np.zeros(0, np.uint8))
     assert oracle.decode(a).size == 0
