@@ -815,9 +815,13 @@ def run_reference(args):
     total = sum(ts)
     v = data.size * args.steps / total / 1e9
     cores = len(os.sched_getaffinity(0))
+    size = args.size or (1 << 30)
+    names = {"fastq": f"paired-end FASTQ {size} bytes, {1 << args.log2_block}-byte blocks, whole-file decode",
+             "genome": f"FASTA genome {args.size or 50_000_000_000} bytes, D = 1 GiB, streamed through a device ring",
+             "tiny": "tiny FASTQ, 2,000 reads"}
     line = base_line(args, v, 1e3 * total / args.steps, args.gpus,
-                     {"workload": f"{args.workload}: first {data.size} bytes of the workload per step",
-                      "log2_block": args.log2_block},
+                     {"workload": names.get(args.workload, args.workload), "log2_block": args.log2_block,
+                      "sample": f"each step decodes the first {data.size} bytes of the workload"},
                      impl="reference",
                      cpu_baseline={"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
                                    "sample": f"first {data.size} bytes of the workload per step; host has {cores} cores"},
