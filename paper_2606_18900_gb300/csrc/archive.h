@@ -5,6 +5,8 @@
 
 #include <cstdint>
 #include <cstring>
+#include <memory>
+#include <new>
 #include <vector>
 
 #include "aceapex.h"
@@ -79,6 +81,23 @@ struct Staging {
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? ACEAPEX_OK : ACEAPEX_ECUDA; }
 
+// host array whose storage is not initialised on allocation (the archive's
+// index sections are copied into it once, in parallel pieces)
+template <class T>
+struct HostArray {
+  std::unique_ptr<T[]> p;
+  uint64_t n = 0;
+  bool alloc(uint64_t count) {
+    p.reset(count ? new (std::nothrow) T[count] : nullptr);
+    n = count;
+    return !count || p != nullptr;
+  }
+  T &operator[](uint64_t i) { return p[i]; }
+  const T &operator[](uint64_t i) const { return p[i]; }
+  T *data() { return p.get(); }
+  uint64_t size() const { return n; }
+};
+
 }  // namespace aceapex
 
 // (internal header: the handle's members use the library namespace)
@@ -88,9 +107,9 @@ struct aceapex_archive {
   int device = 0;
   Header h{};
   std::vector<SegRec> dir;
-  std::vector<uint64_t> dep_ptr;
-  std::vector<uint32_t> deps;
-  std::vector<uint64_t> reads;
+  HostArray<uint64_t> dep_ptr;
+  HostArray<uint32_t> deps;
+  HostArray<uint64_t> reads;
   aceapex_stats stats{};
 
   DBuf<uint8_t> d_payload;

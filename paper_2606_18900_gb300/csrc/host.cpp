@@ -5,11 +5,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "archive.h"
@@ -50,6 +52,24 @@ uint32_t *global_epoch(int device) {
 namespace aceapex {
 
 // FORMAT.md §6 host-side checks; fills h, dir, dep_ptr, deps, reads, stats.
+// f(0) .. f(n - 1) on up to 16 host threads
+template <class F>
+void parallel_for(uint64_t n, F f) {
+  const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  const uint64_t nt = std::min<uint64_t>(n, hw);
+  if (nt <= 1) {
+    for (uint64_t k = 0; k < n; ++k) f(k);
+    return;
+  }
+  std::atomic<uint64_t> next{0};
+  std::vector<std::thread> ts;
+  for (uint64_t t = 0; t < nt; ++t)
+    ts.emplace_back([&] {
+      for (uint64_t k; (k = next.fetch_add(1)) < n;) f(k);
+    });
+  for (auto &t : ts) t.join();
+}
+
 int validate(const uint8_t *a, uint64_t len, aceapex_archive *A) {
   if (len < kHeaderBytes + kTablesBytes || std::memcmp(a, "ACEAPEX1", 8) != 0) return ACEAPEX_ECORRUPT;
   if (rd<uint32_t>(a + 8) != 1 || rd<uint32_t>(a + 12) != kHeaderBytes) return ACEAPEX_ECORRUPT;
@@ -111,28 +131,58 @@ int validate(const uint8_t *a, uint64_t len, aceapex_archive *A) {
     max_lv = std::max<uint32_t>(max_lv, r.level);
   }
   if (po != h.payload_bytes) return ACEAPEX_ECORRUPT;
-  // dependency lists, ascending, below their segment, level consistent
-  A->dep_ptr.resize(h.n_seg + 1);
+  // dependency lists (ascending, below their segment, level consistent) and
+  // the read index (ascending, below N): copied and checked in parallel
+  // pieces, since at gigabyte sizes these are millions of entries
+  std::vector<uint8_t> lvl(h.n_seg);
+  for (uint64_t s = 0; s < h.n_seg; ++s) lvl[s] = (uint8_t)std::min<uint32_t>(A->dir[s].level, 255);
+  if (!A->dep_ptr.alloc(h.n_seg + 1) || !A->deps.alloc(h.n_deps) || !A->reads.alloc(h.n_reads))
+    return ACEAPEX_ENOMEM;
   std::memcpy(A->dep_ptr.data(), a + h.off_dep_ptr, 8 * (h.n_seg + 1));
-  A->deps.resize(h.n_deps);
-  if (h.n_deps) std::memcpy(A->deps.data(), a + h.off_deps, 4 * h.n_deps);
   if (A->dep_ptr[0] != 0 || A->dep_ptr[h.n_seg] != h.n_deps) return ACEAPEX_ECORRUPT;
-  for (uint64_t s = 0; s < h.n_seg; ++s) {
-    uint64_t b = A->dep_ptr[s], e = A->dep_ptr[s + 1];
-    if (e < b || e > h.n_deps) return ACEAPEX_ECORRUPT;
-    uint32_t lv = 0;
-    for (uint64_t i = b; i < e; ++i) {
-      uint32_t d = A->deps[i];
-      if (d >= s || (i > b && d <= A->deps[i - 1])) return ACEAPEX_ECORRUPT;
-      lv = std::max<uint32_t>(lv, A->dir[d].level + 1u);
+  for (uint64_t s = 0; s < h.n_seg; ++s)
+    if (A->dep_ptr[s + 1] < A->dep_ptr[s]) return ACEAPEX_ECORRUPT;
+  const uint64_t seg_per = std::max<uint64_t>(4096, (h.n_seg + 63) / 64);
+  const uint64_t seg_pieces = (h.n_seg + seg_per - 1) / seg_per;
+  const uint64_t read_per = std::max<uint64_t>(1 << 16, (h.n_reads + 63) / 64);
+  const uint64_t read_pieces = (h.n_reads + read_per - 1) / read_per;
+  std::vector<uint8_t> bad(seg_pieces + read_pieces, 0);
+  parallel_for(seg_pieces + read_pieces, [&](uint64_t k) {
+    if (k < seg_pieces) {
+      const uint64_t s0 = k * seg_per, s1 = std::min(h.n_seg, s0 + seg_per);
+      const uint64_t b0 = A->dep_ptr[s0], b1 = A->dep_ptr[s1];
+      if (b1 > b0) std::memcpy(A->deps.data() + b0, a + h.off_deps + 4 * b0, 4 * (b1 - b0));
+      for (uint64_t s = s0; s < s1; ++s) {
+        const uint64_t b = A->dep_ptr[s], e = A->dep_ptr[s + 1];
+        uint32_t lv = 0;
+        for (uint64_t i = b; i < e; ++i) {
+          const uint32_t d = A->deps[i];
+          if (d >= s || (i > b && d <= A->deps[i - 1])) {
+            bad[k] = 1;
+            return;
+          }
+          lv = std::max<uint32_t>(lv, lvl[d] + 1u);
+        }
+        if (lv != A->dir[s].level) {
+          bad[k] = 1;
+          return;
+        }
+      }
+    } else {
+      const uint64_t r0 = (k - seg_pieces) * read_per, r1 = std::min(h.n_reads, r0 + read_per);
+      std::memcpy(A->reads.data() + r0, a + h.off_reads + 8 * r0, 8 * (r1 - r0));
+      uint64_t prev = r0 ? rd<uint64_t>(a + h.off_reads + 8 * (r0 - 1)) : 0;
+      for (uint64_t r = r0; r < r1; ++r) {
+        if (A->reads[r] >= h.n || (r && A->reads[r] <= prev)) {
+          bad[k] = 1;
+          return;
+        }
+        prev = A->reads[r];
+      }
     }
-    if (lv != A->dir[s].level) return ACEAPEX_ECORRUPT;
-  }
-  // read index
-  A->reads.resize(h.n_reads);
-  if (h.n_reads) std::memcpy(A->reads.data(), a + h.off_reads, 8 * h.n_reads);
-  for (uint64_t r = 0; r < h.n_reads; ++r)
-    if (A->reads[r] >= h.n || (r && A->reads[r] <= A->reads[r - 1])) return ACEAPEX_ECORRUPT;
+  });
+  for (uint8_t b : bad)
+    if (b) return ACEAPEX_ECORRUPT;
 
   aceapex_stats &st = A->stats;
   st.decoded_bytes = h.n;
