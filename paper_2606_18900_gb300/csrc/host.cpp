@@ -381,22 +381,40 @@ int aceapex_open(const void *h_archive, uint64_t nbytes, int device, aceapex_arc
   aceapex_archive *A = new (std::nothrow) aceapex_archive();
   if (!A) return ACEAPEX_ENOMEM;
   const uint8_t *a = static_cast<const uint8_t *>(h_archive);
-  int rc = validate(a, nbytes, A);
-  if (rc) {
-    delete A;
-    return rc;
-  }
   A->device = device;
-  if (cudaSetDevice(device) != cudaSuccess) {
+  const bool dev_ok = cudaSetDevice(device) == cudaSuccess;  // reported after validation
+  // The payload (almost all of the archive) goes to the device while the
+  // host checks the rest: its place and size come from the header, checked
+  // against the buffer size first; the copy is waited for before any return.
+  uint64_t pay_off = 0, pay_bytes = 0;
+  if (nbytes >= kHeaderBytes) {
+    pay_off = rd<uint64_t>(a + 104);
+    pay_bytes = rd<uint64_t>(a + 112);
+    if (pay_off > nbytes || pay_bytes > nbytes - pay_off) pay_off = pay_bytes = 0;
+  }
+  cudaStream_t up = nullptr;
+  bool uploading = false;
+  if (dev_ok && pay_bytes && cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking) == cudaSuccess &&
+      A->d_payload.alloc(pay_bytes) == cudaSuccess &&
+      cudaMemcpyAsync(A->d_payload.p, a + pay_off, pay_bytes, cudaMemcpyHostToDevice, up) == cudaSuccess)
+    uploading = true;
+  int rc = validate(a, nbytes, A);
+  const bool upload_ok = !uploading || cudaStreamSynchronize(up) == cudaSuccess;
+  if (up) cudaStreamDestroy(up);
+  if (rc || !upload_ok || !dev_ok) {
+    A->release();
     delete A;
-    return ACEAPEX_ECUDA;
+    return rc ? rc : ACEAPEX_ECUDA;
   }
   std::vector<uint32_t> lut;
   build_lut(a, lut);
   std::vector<WorkItem> order;
   level_order(A->dir, nullptr, A->h.n_seg, 0, order);
   const Header &h = A->h;
-  bool okm = A->d_payload.alloc(std::max<uint64_t>(h.payload_bytes, 16)) == cudaSuccess &&
+  // (the payload buffer is the uploaded one when the header's payload fields
+  // were what validation accepted, else it is allocated and copied now)
+  const bool have_payload = uploading && pay_off == h.off_payload && pay_bytes == h.payload_bytes;
+  bool okm = (have_payload || A->d_payload.alloc(std::max<uint64_t>(h.payload_bytes, 16)) == cudaSuccess) &&
              A->d_dir.alloc(std::max<uint64_t>(h.n_seg, 1)) == cudaSuccess &&
              A->d_lut.alloc(4 * kScale) == cudaSuccess && A->d_flags.alloc(std::max<uint64_t>(h.n_seg, 1)) == cudaSuccess &&
              A->d_order.alloc(std::max<uint64_t>(h.n_seg, 1)) == cudaSuccess && A->d_words.alloc(4) == cudaSuccess &&
@@ -407,7 +425,8 @@ int aceapex_open(const void *h_archive, uint64_t nbytes, int device, aceapex_arc
     return ACEAPEX_ENOMEM;
   }
   cudaError_t e = cudaSuccess;
-  if (h.payload_bytes) e = cudaMemcpy(A->d_payload.p, a + h.off_payload, h.payload_bytes, cudaMemcpyHostToDevice);
+  if (h.payload_bytes && !have_payload)
+    e = cudaMemcpy(A->d_payload.p, a + h.off_payload, h.payload_bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && h.n_seg) e = cudaMemcpy(A->d_dir.p, A->dir.data(), 24 * h.n_seg, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(A->d_lut.p, lut.data(), 4 * lut.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && h.n_seg)
