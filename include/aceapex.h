@@ -98,6 +98,19 @@ int aceapex_level_counts(const aceapex_archive *a, uint64_t *h_counts, uint32_t 
 int aceapex_decode_all(aceapex_archive *a, void *d_out, uint64_t out_cap, void *stream, aceapex_stats *opt_stats);
 
 /*
+ * Whole-file decode into host memory (paper §3.3's end-to-end measurement
+ * over the host link): the archive decodes into a device buffer owned by the
+ * handle, in windows of `window` bytes (0: 256 MiB; rounded to whole
+ * segments) taken in order, and each window is copied to h_out[0..N) on a
+ * second stream while the next one decodes. A window's segments read only
+ * segments of the same or earlier windows, which are complete by then.
+ * h_out should be pinned host memory for the copies to overlap. Stream-
+ * ordered: work on `stream` after this call starts after the last copy.
+ * Errors: EINVAL, ERANGE (out_cap < N), ENOMEM, ECUDA.
+ */
+int aceapex_decode_all_to_host(aceapex_archive *a, void *h_out, uint64_t out_cap, uint64_t window, void *stream);
+
+/*
  * Range decode (paper §4, "v7-RA"): write exactly the bytes [byte_lo,
  * byte_hi) of the decompressed output to d_out[0 .. byte_hi - byte_lo).
  * Decodes only the covering segments and their transitive source closure

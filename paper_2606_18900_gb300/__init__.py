@@ -142,6 +142,7 @@ def lib():
             L.aceapex_free.restype = None
             L.aceapex_fastq_index.argtypes = [vp, u64, u64p, u64]
             L.aceapex_fastq_index.restype = u64
+            L.aceapex_decode_all_to_host.argtypes = [vp, vp, u64, u64, vp]
             L.aceapex_fastq_split.argtypes = [vp, u64, vp, u64p]
             L.aceapex_fastq_split.restype = u64
             L.aceapex_decode_fastq_streams.argtypes = [ctypes.POINTER(vp), vp, u64, vp]
@@ -306,6 +307,13 @@ class Archive:
         cap = out.numel() * out.element_size() if hasattr(out, "numel") else int(out[1])
         _check(lib().aceapex_decode_all(self._h, _ptr(out if hasattr(out, "numel") else out[0]), cap,
                                         _stream(stream), None), "aceapex_decode_all")
+
+    def decode_all_to_host(self, host_out, window: int = 0, stream=None):
+        """Decode the whole archive into a (preferably pinned) host tensor,
+        copying windows out while the next ones decode (async)."""
+        cap = host_out.numel() * host_out.element_size()
+        _check(lib().aceapex_decode_all_to_host(self._h, host_out.data_ptr(), cap, window, _stream(stream)),
+               "aceapex_decode_all_to_host")
 
     def decode_range(self, lo: int, hi: int, out, stream=None):
         cap = out.numel() * out.element_size()

@@ -145,6 +145,13 @@ struct aceapex_archive {
   DBuf<DevArchive> d_batch_arcs;
   DBuf<OutView> d_batch_views;
   Staging stage_batch;
+  // decode to host: device output buffer, window work lists, copy stream
+  DBuf<uint8_t> d_host_out;
+  DBuf<WorkItem> d_win_work;
+  std::vector<uint64_t> win_start;  // work-list offset of each window
+  uint64_t win_bytes = 0;
+  cudaStream_t copy_st = nullptr;
+  std::vector<cudaEvent_t> win_ev;
   // FASTQ stream reassembly (when this handle is a set's first part)
   DBuf<uint8_t> d_fq_streams;
   DBuf<uint32_t> d_fq_counts, d_fq_nl;
@@ -176,6 +183,11 @@ struct aceapex_archive {
     d_words.release(); d_blocked.release(); d_scratch.release(); d_page.release(); d_arena.release();
     d_work.release(); d_ring.release(); d_seg_crc.release(); d_batch_arcs.release(); d_batch_views.release();
     d_fq_streams.release(); d_fq_counts.release(); d_fq_nl.release(); d_fq_offs.release();
+    d_host_out.release(); d_win_work.release();
+    for (cudaEvent_t e : win_ev) cudaEventDestroy(e);
+    win_ev.clear();
+    if (copy_st) cudaStreamDestroy(copy_st);
+    copy_st = nullptr;
     stage_work.release();
     stage_batch.release();
   }

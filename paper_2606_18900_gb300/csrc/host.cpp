@@ -487,6 +487,76 @@ int aceapex_decode_all(aceapex_archive *a, void *d_out, uint64_t out_cap, void *
   return cuda_status(launch_decode(L, a->grid, kBlock, st));
 }
 
+int aceapex_decode_all_to_host(aceapex_archive *a, void *h_out, uint64_t out_cap, uint64_t window, void *stream) {
+  if (!a || (!h_out && a->h.n)) return ACEAPEX_EINVAL;
+  if (out_cap < a->h.n) return ACEAPEX_ERANGE;
+  if (a->h.n == 0) return ACEAPEX_OK;
+  const uint64_t S = uint64_t(1) << a->h.log2_S;
+  if (window == 0) window = uint64_t(256) << 20;
+  window = std::max<uint64_t>(S, window / S * S);
+  if (cudaSetDevice(a->device) != cudaSuccess) return ACEAPEX_ECUDA;
+  int rc = ensure_scratch(a);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (a->d_host_out.n < a->h.n) {
+    cudaStreamSynchronize(st);
+    if (a->d_host_out.alloc(a->h.n) != cudaSuccess) return ACEAPEX_ENOMEM;
+  }
+  if (!a->copy_st && cudaStreamCreateWithFlags(&a->copy_st, cudaStreamNonBlocking) != cudaSuccess)
+    return ACEAPEX_ECUDA;
+  // work lists of the windows, each in level order (built once per window size)
+  if (a->win_bytes != window) {
+    cudaStreamSynchronize(st);
+    std::vector<WorkItem> work;
+    std::vector<uint32_t> segs;
+    a->win_start.clear();
+    for (uint64_t lo = 0; lo < a->h.n; lo += window) {
+      segs.clear();
+      const uint64_t s1 = std::min(a->h.n_seg, (lo + window) / S + ((lo + window) % S ? 1 : 0));
+      for (uint64_t s = lo / S; s < s1; ++s) segs.push_back((uint32_t)s);
+      a->win_start.push_back(work.size());
+      level_order(a->dir, segs.data(), segs.size(), 0, work);
+    }
+    a->win_start.push_back(work.size());
+    if (a->d_win_work.alloc(work.size()) != cudaSuccess ||
+        cudaMemcpy(a->d_win_work.p, work.data(), sizeof(WorkItem) * work.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+      return ACEAPEX_ENOMEM;
+    a->win_bytes = window;
+  }
+  const size_t nwin = a->win_start.size() - 1;
+  while (a->win_ev.size() < nwin + 1) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return ACEAPEX_ECUDA;
+    a->win_ev.push_back(e);
+  }
+  uint32_t *ge = global_epoch(a->device);
+  if (!ge) return ACEAPEX_ECUDA;
+  // the copy stream starts after the caller's earlier work
+  cudaError_t e = cudaEventRecord(a->win_ev[nwin], st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(a->copy_st, a->win_ev[nwin], 0);
+  DecodeLaunch L = base_launch(a);
+  L.view0 = linear_view(a->d_host_out.p, 0);
+  uint8_t *host = static_cast<uint8_t *>(h_out);
+  // window k decodes on `stream` (its sources lie in windows <= k, already
+  // complete with this call's epoch) while window k - 1 is copied out
+  for (size_t k = 0; k < nwin && e == cudaSuccess; ++k) {
+    e = k == 0 ? launch_begin(ge, a->epoch(), a->counter(), st) : cudaMemsetAsync(a->counter(), 0, 4, st);
+    if (e != cudaSuccess) break;
+    L.work = a->d_win_work.p + a->win_start[k];
+    L.n_work = (uint32_t)(a->win_start[k + 1] - a->win_start[k]);
+    if ((e = launch_decode(L, a->grid, kBlock, st)) != cudaSuccess) break;
+    if ((e = cudaEventRecord(a->win_ev[k], st)) != cudaSuccess) break;
+    if ((e = cudaStreamWaitEvent(a->copy_st, a->win_ev[k], 0)) != cudaSuccess) break;
+    const uint64_t lo = (uint64_t)k * window, hi = std::min(a->h.n, lo + window);
+    e = cudaMemcpyAsync(host + lo, a->d_host_out.p + lo, hi - lo, cudaMemcpyDeviceToHost, a->copy_st);
+  }
+  // the caller's stream waits for the last copy
+  if (e == cudaSuccess) e = cudaEventRecord(a->win_ev[nwin], a->copy_st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, a->win_ev[nwin], 0);
+  return cuda_status(e);
+}
+
 int aceapex_decode_range(aceapex_archive *a, uint64_t lo, uint64_t hi, void *d_out, uint64_t out_cap, void *stream) {
   if (!a || (!d_out && hi > lo)) return ACEAPEX_EINVAL;
   if (lo > hi || hi > a->h.n || out_cap < hi - lo) return ACEAPEX_ERANGE;

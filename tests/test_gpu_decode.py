@@ -234,6 +234,23 @@ def test_fastq_stream_separation_round_trip(cut):
         p.close()
 
 
+@pytest.mark.parametrize("window", [0, 1, 16384 * 7, 1 << 22])
+def test_decode_all_to_host_windows(window):
+    """Decode straight to pinned host memory in windows copied out while the
+    next ones decode: the bytes equal the source for any window size (a
+    window below a segment is one segment), twice in a row on one handle."""
+    d = synth.pe_fastq(8 << 20, ref_len=2_000_000)
+    a = ace.encode(d, min_match=16)
+    with ace.Archive(a) as arc:
+        for _ in range(2):
+            host = torch.zeros(d.size, dtype=torch.uint8).pin_memory()
+            s = torch.cuda.Stream()
+            arc.decode_all_to_host(host, window, s)
+            s.synchronize()
+            arc.check(s)
+            assert_same(host.numpy(), d)
+
+
 def test_level_counts_match_directory():
     d = synth.pe_fastq(2 << 20, ref_len=500_000)
     a = ace.encode(d, min_match=12, max_level=5)
