@@ -569,7 +569,7 @@ int aceapex_decode_range(aceapex_archive *a, uint64_t lo, uint64_t hi, void *d_o
   uint32_t n = 0;
   rc = decode_closure(a, lo >> a->h.log2_S, (hi - 1) >> a->h.log2_S, st, &v, &n, true);
   if (rc) return rc;
-  cudaError_t e = launch_gather(v, a->h.log2_S, lo, hi, static_cast<uint8_t *>(d_out) - 0, st);
+  cudaError_t e = launch_gather(v, a->h.log2_S, lo, hi, static_cast<uint8_t *>(d_out), st);
   if (e == cudaSuccess) e = launch_clear_pages(a->d_page.p, a->d_work.p, n, st);
   return cuda_status(e);
 }
