@@ -332,3 +332,48 @@ def test_wavefront_decoder_equals_sequential():
         a = ace.encode(d, **kw)
         for t in (1, 3, 8):
             assert np.array_equal(oracle.decode_wavefront(a, t), d)
+
+
+def _rans_decode_py(a: np.ndarray, sec: dict, seg: int):
+    """rANS decode of one segment written out from the definition (Duda,
+    arXiv:1311.2540; the interleaving rule of the format): symbol q belongs to
+    lane q mod 32 and class c(q); slot = x mod 4096 selects the symbol s with
+    cum[s] <= slot < cum[s] + f[s]; x <- f[s] * (x div 4096) + slot - cum[s];
+    while x < 2^16 the lane shifts in the next 16-bit word."""
+    d = sec["dir"][seg]
+    nc, nl, nw, W = int(d["n_cmd"]), int(d["n_lit"]), int(d["n_words"]), int(sec["W"])
+    n_sym = (4 + W) * nc + nl
+    base = sec["off_payload"] + int(d["payload_off"])
+    x = [int.from_bytes(a[base + 4 * j: base + 4 * j + 4].tobytes(), "little") for j in range(32)]
+    words = a[base + 128: base + 128 + 2 * nw].view("<u2").astype(np.int64)
+    freq = sec["tables"].astype(np.int64)
+    cum = np.concatenate([np.zeros((4, 1), np.int64), np.cumsum(freq, axis=1)], axis=1)
+    out = np.empty(n_sym, np.uint8)
+    p = 0
+    for q in range(n_sym):
+        j = q % 32
+        c = 0 if q < 2 * nc else 1 if q < 4 * nc else 2 if q < (4 + W) * nc else 3
+        slot = x[j] % 4096
+        sym = int(np.searchsorted(cum[c], slot, side="right")) - 1
+        out[q] = sym
+        x[j] = int(freq[c, sym]) * (x[j] // 4096) + slot - int(cum[c, sym])
+        if x[j] < (1 << 16):
+            x[j] = (x[j] << 16) + int(words[p])
+            p += 1
+    return out, x, p
+
+
+def test_rans_against_an_independent_decoder():
+    """The oracle's rANS (C) and a plain Python decoder written from the rANS
+    definition give the same symbols, the final states 2^16 and every word
+    consumed, on segments of archives from both encoders."""
+    import paper_2606_18900_gb300 as ace
+    d = synth.tiny_fastq()[:120_000]
+    for a in (oracle.encode(d), ace.encode(d, min_match=16)):
+        sec = oracle.sections(a)
+        for seg in range(sec["n_segments"]):
+            rc, cmds, sym, states = oracle.segment_info(a, seg)
+            assert rc == 0
+            got, x, p = _rans_decode_py(a, sec, seg)
+            assert np.array_equal(got, sym), seg
+            assert x == [1 << 16] * 32 and p == int(sec["dir"][seg]["n_words"])
