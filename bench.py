@@ -43,7 +43,8 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="fastq", choices=["fastq", "tiny", "batch", "genome", "serve", "entropy", "fastq_streams"])
+    p.add_argument("--workload", default="fastq", choices=["fastq", "tiny", "batch", "genome", "serve", "entropy", "fastq_streams",
+                                                         "encode"])
     p.add_argument("--log2-block", type=int, default=14)
     p.add_argument("--size", type=int, default=0, help="workload bytes (0 = the workload's default)")
     p.add_argument("--min-match", type=int, default=0, help="0 = the workload's default")
@@ -522,6 +523,113 @@ def workload_fastq_streams(args):
         p_.close()
 
 
+# ------------------------------------------------------------------ encode
+
+def workload_encode(args):
+    """The GPU encoder on the paired-end FASTQ (1 GiB, 16 KiB blocks,
+    min_match 16, read index). value: input bytes encoded per second with the
+    input resident in device memory (device time of each call up to the
+    archive's copy-out, CUDA events on the encoder's stream); e2e: host input
+    to host archive through the public call. Beside it the library's CPU
+    encoder on every host core, whose archive must be identical, and the
+    oracle's encoder on a bounded sample."""
+    import torch
+
+    import oracle
+    import paper_2606_18900_gb300 as ace
+    import synth
+
+    size = args.size or (1 << 30)
+    mm = args.min_match or 16
+    data = synth.pe_fastq(size)
+    N = data.size
+    reads = ace.fastq_index(data)
+    d_in = torch.from_numpy(data).cuda()
+    enc = ace.GpuEncoder(0)
+    kw = dict(log2_B=args.log2_block, min_match=mm, reads=reads)
+    for _ in range(args.warmup):
+        arc = enc.encode(d_in, **kw)
+    clocks = Clocks(0)
+    clocks.start()
+    stats = []
+    for _ in range(args.steps):
+        arc = enc.encode(d_in, **kw)
+        stats.append(dict(enc.last_stats))
+    clk = clocks.stop()
+    dev_ms = [s_["ms_total"] - s_["ms_d2h"] for s_ in stats]
+    total_ms = float(sum(dev_ms))
+    value = N * args.steps / (total_ms * 1e-3) / 1e9
+
+    h_in = torch.from_numpy(data).pin_memory().numpy()
+    ts = []
+    for _ in range(3):
+        t = time.perf_counter()
+        a2 = enc.encode(h_in, **kw)
+        ts.append(time.perf_counter() - t)
+    if a2.tobytes() != arc.tobytes():
+        raise SystemExit("bench: host-input and device-input encodes differ")
+    e2e = {"value": N / float(np.mean(ts)) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(N),
+           "d2h_bytes_per_step": int(arc.size), "steps": len(ts),
+           "what": "GpuEncoder.encode of a pinned host array, archive returned in host memory"}
+
+    t = time.perf_counter()
+    host = ace.encode(data, **kw)
+    host_s = time.perf_counter() - t
+    identical = host.tobytes() == arc.tobytes()
+    if not identical:
+        raise SystemExit("bench: GPU archive differs from the CPU encoder's")
+    with ace.Archive(arc) as a:
+        st = a.stats()
+        out = torch.empty(N, dtype=torch.uint8, device="cuda")
+        a.decode_all(out)
+        a.check()
+        round_trip = bool(np.array_equal(out.cpu().numpy(), data))
+    if not round_trip:
+        raise SystemExit("bench: GPU decode of the GPU archive differs from the input")
+
+    cpu = None
+    if not args.no_cpu:
+        sample = data[: 8 << 20]
+        t = time.perf_counter()
+        oarc = oracle.encode(sample, log2_B=args.log2_block, min_match=mm)
+        o_s = time.perf_counter() - t
+        cpu = {"value": sample.size / o_s / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"the oracle's encoder on the first {sample.size} bytes of the workload ({o_s:.1f} s)",
+               "round_trip": bool(np.array_equal(oracle.decode(oarc), sample)),
+               "library_cpu_encoder": {"value": N / host_s / 1e9, "unit": "GB/s",
+                                       "cores": len(os.sched_getaffinity(0)), "seconds": round(host_s, 2),
+                                       "kind": "aceapex_encode on every host core (same archive)"}}
+
+    pk = [s_["ms_parse_kernel"] / max(1, s_["parse_launches"]) for s_ in stats]
+    parse_ms = float(np.mean(pk))
+    n_cmd = st["n_commands"]
+    alg = N + 4 * N + 14 * n_cmd  # input and chain links read once, commands written
+    peak, peak_kind = read_peaks()
+    achieved = alg / (parse_ms * 1e-3) / 1e9
+    mean = lambda k: float(np.mean([s_[k] for s_ in stats]))
+    line = base_line(
+        args, value, total_ms / args.steps, 1,
+        {"workload": f"GPU encode of paired-end FASTQ {N} bytes, {1 << args.log2_block}-byte blocks, min_match {mm},"
+                     " read index", "log2_block": args.log2_block, "min_match": mm,
+         "ratio": round(N / arc.size, 3), "archive_bytes": int(arc.size), "n_commands": int(n_cmd),
+         "l2": "inputs larger than L2 (1 GiB input, 24 GiB of chain arrays)",
+         "phase_ms": {"chains": mean("ms_chains"), "parse_kernel": mean("ms_parse_kernel"),
+                      "symbols_levels_deps": mean("ms_parse") - mean("ms_parse_kernel"),
+                      "entropy_and_layout": mean("ms_entropy"), "h2d_copy": mean("ms_h2d"),
+                      "archive_d2h": mean("ms_d2h")},
+         "identical_to_cpu_encoder": identical, "round_trip": round_trip},
+        metric="encoded input GB/s, input resident in device memory",
+        roofline={"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                  "peak_kind": peak_kind, "kernel": "enc_parse_kernel",
+                  "bytes_model": "N input + 4N chain links read once + 14 B per command written",
+                  "algorithmic_bytes": int(alg), "traffic": None,
+                  "note": "chain walks are dependent random loads: latency-bound, not bandwidth-bound"},
+        cpu_baseline=cpu, e2e=e2e, gpu_launches=int(sum(s_["kernel_launches"] for s_ in stats)), clocks=clk,
+        bit_exact=identical and round_trip, ms_median=float(np.median(dev_ms)))
+    print(json.dumps(line), flush=True)
+    enc.close()
+
+
 # ------------------------------------------------------------------- batch
 
 def workload_batch(args):
@@ -847,6 +955,8 @@ def main():
         workload_entropy(args)
     elif args.workload == "fastq_streams":
         workload_fastq_streams(args)
+    elif args.workload == "encode":
+        workload_encode(args)
     else:
         workload_genome(args)
 

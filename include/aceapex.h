@@ -334,6 +334,50 @@ uint64_t aceapex_fastq_split(const void *h_in, uint64_t n, void *h_out, uint64_t
  */
 int aceapex_decode_fastq_streams(aceapex_archive *const *parts, void *d_out, uint64_t out_cap, void *stream);
 
+/*
+ * GPU encoder (paper §2's global match search run on the device; the paper's
+ * encoder is CPU-only and is the bottleneck it names in §8). It applies the
+ * rules of aceapex_encode (same hash, chain depth, level schedule, parse and
+ * tables) and returns the same archive, byte for byte.
+ *
+ * aceapex_gpu_encoder_create binds an encoder to a device; it owns a CUDA
+ * stream and device scratch that grows on demand and is kept between calls
+ * (about 24 bytes per position of a chain window, n bytes of symbols, the
+ * archive). aceapex_gpu_encoder_destroy frees it all. Errors: EINVAL,
+ * ENOMEM, ECUDA.
+ */
+typedef struct aceapex_gpu_encoder aceapex_gpu_encoder;
+
+/* Device times of one aceapex_gpu_encode call (CUDA events on its stream). */
+typedef struct {
+  double ms_total;    /* input copy to archive copy-out, inclusive */
+  double ms_h2d;      /* input copy into the encoder's padded buffer */
+  double ms_chains;   /* hashing, radix sort, links (all windows) */
+  double ms_parse;    /* parse, flattening, dependency lists, symbols, levels (all windows) */
+  double ms_parse_kernel; /* the parse kernel's launches alone (part of ms_parse) */
+  double ms_entropy;  /* tables, rANS (two passes), directory and sections */
+  double ms_d2h;      /* archive copy to host memory */
+  uint64_t input_bytes, archive_bytes, n_segments, n_deps, windows, parse_launches;
+  uint64_t kernel_launches; /* kernels the call launched */
+} aceapex_encode_stats;
+
+int aceapex_gpu_encoder_create(int device, aceapex_gpu_encoder **out);
+void aceapex_gpu_encoder_destroy(aceapex_gpu_encoder *enc);
+
+/*
+ * Encode in[0..n) (host memory, or device memory of the encoder's device when
+ * in_on_device != 0) into a FORMAT.md v1 archive returned in a malloc'd host
+ * buffer *h_out of *out_len bytes (free with aceapex_free). Parameters and
+ * their limits are those of aceapex_encode (n < 2^32 when dist_bound = 0,
+ * dist_bound < 2^31). Synchronous: returns when the archive is in host
+ * memory. opt_stats (may be NULL) receives the phase times. Errors: EINVAL,
+ * ENOMEM, ECUDA, ECORRUPT (an internal invariant of the encoder failed; no
+ * archive is returned).
+ */
+int aceapex_gpu_encode(aceapex_gpu_encoder *enc, const void *in, int in_on_device, uint64_t n, uint32_t log2_B,
+                       uint32_t min_match, uint32_t max_level, uint64_t dist_bound, const uint64_t *h_reads,
+                       uint64_t n_reads, void **h_out, uint64_t *out_len, aceapex_encode_stats *opt_stats);
+
 #ifdef __cplusplus
 }
 #endif

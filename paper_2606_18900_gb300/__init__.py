@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _SO = os.path.join(_HERE, "libaceapex.so")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
-_SOURCES = ["kernels.cu", "host.cpp", "encoder.cpp", "server.cpp"]
+_SOURCES = ["kernels.cu", "gpu_encoder.cu", "host.cpp", "encoder.cpp", "server.cpp"]
 _lock = threading.Lock()
 _lib = None
 
@@ -45,10 +45,10 @@ def _nvcc() -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile libaceapex.so in-tree for sm_103a (three translation units in
+    """Compile libaceapex.so in-tree for sm_103a (the translation units in
     parallel, then one link)."""
     srcs = [os.path.join(_CSRC, s) for s in _SOURCES]
-    deps = srcs + [os.path.join(_CSRC, h) for h in ("format.h", "kernels.h", "archive.h")] + [os.path.join(_INCLUDE, "aceapex.h")]
+    deps = srcs + [os.path.join(_CSRC, h) for h in ("format.h", "kernels.h", "archive.h", "encoder_rules.h")] + [os.path.join(_INCLUDE, "aceapex.h")]
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(os.path.getmtime(d) for d in deps):
         return _SO
     nvcc = _nvcc()
@@ -82,6 +82,16 @@ class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in ("decoded_bytes", "compressed_bytes", "match_bytes", "literal_bytes",
                                                "n_commands", "n_segments", "n_blocks", "n_deps", "n_reads")] + \
                [(k, ctypes.c_uint32) for k in ("max_level", "log2_B", "log2_S", "W")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class EncodeStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("ms_total", "ms_h2d", "ms_chains", "ms_parse", "ms_parse_kernel",
+                                               "ms_entropy", "ms_d2h")] + \
+               [(k, ctypes.c_uint64) for k in ("input_bytes", "archive_bytes", "n_segments", "n_deps", "windows",
+                                               "parse_launches", "kernel_launches")]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -150,6 +160,13 @@ def lib():
             L.aceapex_fasta_index.restype = u64
             L.aceapex_region_lookup.argtypes = [vp, u64, u64, u64, ctypes.c_uint32, u64p, u64p]
             L.aceapex_decode_region.argtypes = [vp, u64, u64, u64, ctypes.c_uint32, vp, u64, vp]
+            L.aceapex_gpu_encoder_create.argtypes = [i32, ctypes.POINTER(vp)]
+            L.aceapex_gpu_encoder_create.restype = i32
+            L.aceapex_gpu_encoder_destroy.argtypes = [vp]
+            L.aceapex_gpu_encoder_destroy.restype = None
+            L.aceapex_gpu_encode.argtypes = [vp, vp, i32, u64, u32, u32, u32, u64, u64p, u64, ctypes.POINTER(vp), u64p,
+                                             ctypes.POINTER(EncodeStats)]
+            L.aceapex_gpu_encode.restype = i32
             for f in ("aceapex_open", "aceapex_get_stats", "aceapex_decode_all", "aceapex_decode_range",
                       "aceapex_read_lookup", "aceapex_last_error", "aceapex_set_wait_limit",
                       "aceapex_debug_block_segments", "aceapex_stream_range", "aceapex_decode_batch",
@@ -209,6 +226,65 @@ def encode(data, log2_B: int = 14, min_match: int = 0, max_level: int = 8, dist_
     ctypes.memmove(arr.ctypes.data, out.value, n.value)
     L.aceapex_free(out)
     return arr
+
+
+class GpuEncoder:
+    """The GPU encoder on one device: the same archive as encode(), byte for
+    byte, with the match search, parse and entropy coding in CUDA kernels.
+    Keeps its device scratch between calls; close() (or a with block) frees
+    it. last_stats holds the phase times of the latest call."""
+
+    def __init__(self, device: int = 0):
+        self._h = ctypes.c_void_p()
+        _check(lib().aceapex_gpu_encoder_create(int(device), ctypes.byref(self._h)), "aceapex_gpu_encoder_create")
+        self.device = int(device)
+        self.last_stats = None
+
+    def encode(self, data, log2_B: int = 14, min_match: int = 0, max_level: int = 8, dist_bound: int = 0,
+               reads=None) -> np.ndarray:
+        """Archive bytes (uint8 array) of data: a numpy array / bytes in host
+        memory, or a contiguous uint8 torch tensor on this encoder's device."""
+        if not self._h:
+            raise ValueError("encoder is closed")
+        on_dev = hasattr(data, "data_ptr") and getattr(data, "is_cuda", False)
+        if on_dev:
+            if not data.is_contiguous() or data.element_size() != 1:
+                raise ValueError("device input must be a contiguous uint8 tensor")
+            ptr, n, keep = data.data_ptr(), data.numel(), data
+        else:
+            keep = _as_u8(data)
+            ptr, n = (keep.ctypes.data if keep.size else None), keep.size
+        r = np.ascontiguousarray(reads if reads is not None else np.empty(0), dtype=np.uint64)
+        out = ctypes.c_void_p()
+        ln = ctypes.c_uint64()
+        st = EncodeStats()
+        rc = lib().aceapex_gpu_encode(self._h, ptr, 1 if on_dev else 0, n, log2_B, min_match, max_level, dist_bound,
+                                      r.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) if r.size else None, r.size,
+                                      ctypes.byref(out), ctypes.byref(ln), ctypes.byref(st))
+        del keep
+        _check(rc, "aceapex_gpu_encode")
+        arr = np.empty(ln.value, dtype=np.uint8)
+        ctypes.memmove(arr.ctypes.data, out.value, ln.value)
+        lib().aceapex_free(out)
+        self.last_stats = st.as_dict()
+        return arr
+
+    def close(self):
+        if self._h:
+            lib().aceapex_gpu_encoder_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fastq_index(data) -> np.ndarray:

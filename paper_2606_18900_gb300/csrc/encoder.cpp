@@ -26,6 +26,7 @@
 #include <thread>
 #include <vector>
 
+#include "encoder_rules.h"
 #include "format.h"
 
 namespace aceapex {
@@ -42,11 +43,6 @@ struct Geo {
   uint64_t n, S, n_seg, D;
   uint32_t log2_B, log2_S, W, min_match, cap;
 };
-
-inline uint32_t ruler_target(uint64_t s, uint32_t cap) {
-  uint32_t tz = (uint32_t)__builtin_ctzll(s + 1);
-  return cap - std::min(cap, tz);
-}
 
 template <class F>
 void parallel_for(uint64_t n, int threads, F &&f) {
@@ -111,8 +107,7 @@ inline uint32_t hash_at(const uint8_t *p, uint32_t hlen, int kHashBits) {
   uint64_t a = 0, b = 0;
   std::memcpy(&a, p, hlen < 8 ? hlen : 8);
   if (hlen > 8) std::memcpy(&b, p + 8, hlen - 8);
-  uint64_t v = a * 0x9E3779B97F4A7C15ull ^ (b + 0x632BE59BD9B4E019ull) * 0xC2B2AE3D27D4EB4Full;
-  return (uint32_t)((v ^ (v >> 29)) * 0xBF58476D1CE4E5B9ull >> (64 - kHashBits));
+  return hash_words(a, b, kHashBits);
 }
 
 // Chains equal to one sequential insertion pass, built in parallel: hash
@@ -122,8 +117,7 @@ inline uint32_t hash_at(const uint8_t *p, uint32_t hlen, int kHashBits) {
 // owns its head entries, so no two threads touch the same chain.
 void build_chains(Window &w, int threads) {
   const uint64_t len = w.end - w.base;
-  int kHashBits = 16;
-  while (kHashBits < 28 && (uint64_t(1) << kHashBits) < 2 * len) ++kHashBits;
+  const int kHashBits = hash_bits_for(len);
   const uint64_t lim = (w.base + w.hlen <= w.n) ? std::min<uint64_t>(len, w.n - w.hlen + 1 - w.base) : 0;
   w.lim = lim;
   w.prev.reserve(len ? len : 1);
@@ -226,7 +220,7 @@ struct Parser {
       if (L > best) {
         best = L;
         best_src = c;
-        if ((L == lim && lim == seg_end - p) || L >= 256) break;
+        if ((L == lim && lim == seg_end - p) || L >= kGoodEnough) break;
       }
     }
     *src_out = best_src;
@@ -334,31 +328,6 @@ struct Tables {
   uint32_t c[4][257];
 };
 
-void normalize(const uint64_t *cnt, uint16_t *f) {
-  uint64_t total = 0;
-  for (int s = 0; s < 256; ++s) total += cnt[s];
-  std::memset(f, 0, 512);
-  if (!total) return;
-  int64_t sum = 0;
-  for (int s = 0; s < 256; ++s) {
-    if (!cnt[s]) continue;
-    uint64_t v = (uint64_t)(((unsigned __int128)cnt[s] * kScale + total / 2) / total);
-    if (v < 1) v = 1;
-    f[s] = (uint16_t)v;
-    sum += (int64_t)v;
-  }
-  // fix the sum on the symbols with the largest counts (ties: lowest symbol)
-  int order[256];
-  for (int s = 0; s < 256; ++s) order[s] = s;
-  std::stable_sort(order, order + 256, [&](int a, int b) { return cnt[a] > cnt[b]; });
-  int64_t diff = (int64_t)kScale - sum;
-  for (int k = 0; diff != 0; k = (k + 1) % 256) {
-    int s = order[k];
-    if (!cnt[s]) { k = -1; continue; }
-    if (diff > 0) { f[s]++; diff--; }
-    else if (f[s] > 1) { f[s]--; diff++; }
-  }
-}
 
 inline int sym_class(uint64_t q, uint64_t n, uint32_t W) {
   return q < 2 * n ? 0 : q < 4 * n ? 1 : q < (4 + (uint64_t)W) * n ? 2 : 3;
@@ -418,6 +387,32 @@ inline void put64(uint8_t *p, uint64_t v) { std::memcpy(p, &v, 8); }
 
 }  // namespace
 
+void normalize_counts(const uint64_t *cnt, uint16_t *f) {
+  uint64_t total = 0;
+  for (int s = 0; s < 256; ++s) total += cnt[s];
+  std::memset(f, 0, 512);
+  if (!total) return;
+  int64_t sum = 0;
+  for (int s = 0; s < 256; ++s) {
+    if (!cnt[s]) continue;
+    uint64_t v = (uint64_t)(((unsigned __int128)cnt[s] * kScale + total / 2) / total);
+    if (v < 1) v = 1;
+    f[s] = (uint16_t)v;
+    sum += (int64_t)v;
+  }
+  // fix the sum on the symbols with the largest counts (ties: lowest symbol)
+  int order[256];
+  for (int s = 0; s < 256; ++s) order[s] = s;
+  std::stable_sort(order, order + 256, [&](int a, int b) { return cnt[a] > cnt[b]; });
+  int64_t diff = (int64_t)kScale - sum;
+  for (int k = 0; diff != 0; k = (k + 1) % 256) {
+    int s = order[k];
+    if (!cnt[s]) { k = -1; continue; }
+    if (diff > 0) { f[s]++; diff--; }
+    else if (f[s] > 1) { f[s]--; diff++; }
+  }
+}
+
 // Returns 0 or an aceapex_status code. *out is malloc'd.
 int encode_archive(const uint8_t *in, uint64_t n, uint32_t log2_B, uint32_t min_match, uint32_t cap, uint64_t D,
                    const uint64_t *reads, uint64_t n_reads, int threads, uint8_t **out, uint64_t *out_len) {
@@ -442,23 +437,23 @@ int encode_archive(const uint8_t *in, uint64_t n, uint32_t log2_B, uint32_t min_
 
   // ---- parse, window by window
   std::vector<std::vector<Cmd>> cmds(g.n_seg);
-  const uint64_t chunk = D ? std::max<uint64_t>(uint64_t(1) << 30, g.S) : std::max<uint64_t>(n, 1);
+  const uint64_t chunk = D ? std::max<uint64_t>(kDistWindow, g.S) : std::max<uint64_t>(n, 1);
   Window w;
   w.in = in;
   w.n = n;
-  w.hlen = std::min<uint32_t>(g.min_match, 16);
+  w.hlen = hash_len_for(g.min_match);
   // Long minimum matches use content-defined sampling: a position is indexed
   // and probed only when the low bits of its hash are zero (1 in 4), which
   // finds a match of length >= hlen + 15 with probability > 0.99 (a
   // sampled position falls inside its first min_match - hlen + 1 starts) and
   // cuts the indexing and probing work by four.
-  w.sample_mask = g.min_match >= w.hlen + 16 ? 3u : 0u;
+  w.sample_mask = sample_mask_for(g.min_match);
   for (uint64_t a = 0; a < n; a += chunk) {
     uint64_t b = std::min(n, a + chunk);
     w.base = D ? (a > D ? a - D : 0) : 0;
     w.end = b;
     build_chains(w, threads);
-    Parser P{g, w, 16};
+    Parser P{g, w, kChainDepth};
     uint64_t s0 = a >> g.log2_S, s1 = (b + g.S - 1) >> g.log2_S;
     parallel_for(s1 - s0, threads, [&](uint64_t i) { P.parse_segment(s0 + i, cmds[s0 + i]); });
   }
@@ -508,7 +503,7 @@ int encode_archive(const uint8_t *in, uint64_t n, uint32_t log2_B, uint32_t min_
     for (auto &pp : part)
       for (int i = 0; i < 1024; ++i) cnt[i / 256][i % 256] += pp[i];
     for (int c = 0; c < 4; ++c) {
-      normalize(cnt[c], t.f[c]);
+      normalize_counts(cnt[c], t.f[c]);
       t.c[c][0] = 0;
       for (int s = 0; s < 256; ++s) t.c[c][s + 1] = t.c[c][s] + t.f[c][s];
     }
