@@ -342,8 +342,8 @@ int aceapex_decode_fastq_streams(aceapex_archive *const *parts, void *d_out, uin
  *
  * aceapex_gpu_encoder_create binds an encoder to a device; it owns a CUDA
  * stream and device scratch that grows on demand and is kept between calls
- * (about 24 bytes per position of a chain window, n bytes of symbols, the
- * archive). aceapex_gpu_encoder_destroy frees it all. Errors: EINVAL,
+ * (16 bytes per position of a chain window, 8 per position of a parse window,
+ * 16 KiB of symbols per segment, the archive). aceapex_gpu_encoder_destroy frees it all. Errors: EINVAL,
  * ENOMEM, ECUDA.
  */
 typedef struct aceapex_gpu_encoder aceapex_gpu_encoder;
@@ -352,12 +352,12 @@ typedef struct aceapex_gpu_encoder aceapex_gpu_encoder;
 typedef struct {
   double ms_total;    /* input copy to archive copy-out, inclusive */
   double ms_h2d;      /* input copy into the encoder's padded buffer */
-  double ms_chains;   /* hashing, radix sort, links (all windows) */
-  double ms_parse;    /* parse, flattening, dependency lists, symbols, levels (all windows) */
-  double ms_parse_kernel; /* the parse kernel's launches alone (part of ms_parse) */
+  double ms_chains;   /* hashing and radix sort (all windows) */
+  double ms_match;    /* the match-search kernel (all windows) */
+  double ms_parse;    /* match mask, parse, dependency lists, symbols, levels (all windows) */
   double ms_entropy;  /* tables, rANS (two passes), directory and sections */
   double ms_d2h;      /* archive copy to host memory */
-  uint64_t input_bytes, archive_bytes, n_segments, n_deps, windows, parse_launches;
+  uint64_t input_bytes, archive_bytes, n_segments, n_deps, windows;
   uint64_t kernel_launches; /* kernels the call launched */
 } aceapex_encode_stats;
 

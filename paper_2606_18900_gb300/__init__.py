@@ -88,10 +88,10 @@ class Stats(ctypes.Structure):
 
 
 class EncodeStats(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_double) for k in ("ms_total", "ms_h2d", "ms_chains", "ms_parse", "ms_parse_kernel",
+    _fields_ = [(k, ctypes.c_double) for k in ("ms_total", "ms_h2d", "ms_chains", "ms_match", "ms_parse",
                                                "ms_entropy", "ms_d2h")] + \
                [(k, ctypes.c_uint64) for k in ("input_bytes", "archive_bytes", "n_segments", "n_deps", "windows",
-                                               "parse_launches", "kernel_launches")]
+                                               "kernel_launches")]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -216,6 +216,14 @@ struct Parser {
         }
       }
       if (lim <= best) continue;
+      // a longer match than best agrees on bytes [0, best]: the 8 bytes
+      // ending at best decide most losers with one comparison
+      if (best >= 7) {
+        uint64_t x, y;
+        std::memcpy(&x, w.in + c + best - 7, 8);
+        std::memcpy(&y, w.in + p + best - 7, 8);
+        if (x != y) continue;
+      }
       uint64_t L = common_len(w.in + c, w.in + p, lim);
       if (L > best) {
         best = L;

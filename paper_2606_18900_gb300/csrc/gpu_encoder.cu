@@ -5,14 +5,20 @@
 // the host encoder (encoder_rules.h) and writes the same archive, byte for
 // byte, in four phases:
 //
-//  1. chains: hash every position of the chain window, stable LSD radix sort
-//     of (hash, position) pairs, then link each position to the previous one
-//     with the same hash; the links equal those of a sequential insertion
-//     pass over a hash table.
-//  2. parse: one thread per segment (the ruler level schedule makes segments
-//     independent): chain walk, one-step lazy matching, the symbol budget,
-//     flattening of intra-segment chains, and the segment's sorted list of
-//     source segments.
+//  1. chains: hash every position of the chain window and sort the (hash,
+//     position) pairs stably (LSD radix sort); the positions with the same
+//     hash then sit in ascending order, so the slots before a position's
+//     slot are its hash chain, latest first, equal to the chains of a
+//     sequential insertion pass over a hash table.
+//  2. match and parse: one thread per sorted slot finds the longest legal
+//     match of its position among the preceding slots (coalesced reads, no
+//     dependent walk; a candidate whose 8 bytes ending at the current best
+//     length differ cannot win and is not compared further) into a table
+//     indexed by position, with a bitmask of the usable ones; then one
+//     thread per segment (the ruler level schedule
+//     makes segments independent) parses greedily with one-step lazy
+//     matching, jumping between mask bits, applies the symbol budget,
+//     flattens intra-segment chains and lists the segment's source segments.
 //  3. symbols: one warp per segment writes the segment's symbol message
 //     (FORMAT.md §3) and counts symbols per class; levels follow tier by tier
 //     of the schedule (a segment only reads lower tiers); dependency lists
@@ -42,7 +48,7 @@ namespace {
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr uint32_t kInPad = 64;          // readable bytes past the input's end
 constexpr uint32_t kBatchSegs = 65536;   // segments parsed per launch
-constexpr uint32_t kErrCmdCap = 1, kErrLevel = 2, kErrSchedule = 4;
+constexpr uint32_t kErrCmdCap = 1, kErrLevel = 2, kErrSchedule = 4, kErrSymbols = 8;
 
 // ------------------------------------------------------------ shared helpers
 
@@ -82,34 +88,30 @@ ACE_HD uint64_t common_len(const uint8_t *a, const uint8_t *b, uint64_t lim) {
   return L;
 }
 
-// What the parse of one segment reads.
+// What the match search and the parse read.
 struct ParseCtx {
   const uint8_t *in;
   uint64_t n;
-  const uint32_t *prev;  // prev[p - base]: previous position with the same hash (relative + 1), 0 = none
-  const uint32_t *hv;    // hash of each position (sampled mode only)
-  uint64_t base, lim;    // chain window start; positions [base, base + lim) have a full hash window
+  uint64_t base;  // first position of the chain window (sorted values are relative to it)
   uint64_t S, D;
-  uint32_t log2_S, W, min_match, cap, hlen, sample_mask;
+  uint32_t log2_S, W, min_match, cap, sample_mask;
 };
 
-ACE_HD bool sampled(const ParseCtx &g, uint64_t p) {
-  return p >= g.base && p - g.base < g.lim && (g.hv[p - g.base] & g.sample_mask) == 0;
-}
-
-// Longest legal match at p in segment s: walk at most kChainDepth earlier
-// positions with the same hash; a candidate is clipped at the distance
-// bound, at the segment end, at p itself (src + len <= p) and at the first
-// source segment that the level schedule forbids.
-ACE_HD uint64_t find_match(const ParseCtx &g, uint64_t s, uint32_t Ts, uint64_t p, uint64_t seg_end,
-                           uint64_t *src_out) {
-  *src_out = 0;
-  if (p + g.hlen > g.n || p < g.base) return 0;
+// Longest legal match at position p = base + V[j], sorted slot j. The
+// positions with the same hash sit in the slots just before j, latest first
+// (the sort is stable), so they are p's hash chain: at most kChainDepth of
+// them are tried. A candidate is clipped at the distance bound, at the
+// segment end, at p itself (src + len <= p) and at the first source segment
+// that the level schedule forbids.
+ACE_HD uint64_t match_at_slot(const ParseCtx &g, const uint32_t *K, const uint32_t *V, uint64_t j, uint64_t p,
+                              uint64_t *src_out) {
+  const uint64_t s = p >> g.log2_S, seg_end = min64(g.n, (s + 1) << g.log2_S);
+  const uint32_t Ts = ruler_target(s, g.cap), key = K[j];
   uint64_t best = 0, best_src = 0;
-  uint32_t c1 = g.prev[p - g.base];
-  for (uint32_t k = 0; k < kChainDepth && c1 != 0; ++k) {
-    const uint64_t c = g.base + c1 - 1;
-    c1 = g.prev[c - g.base];
+  for (uint32_t k = 0; k < kChainDepth && k < j; ++k) {
+    const uint64_t jj = j - 1 - k;
+    if (K[jj] != key) break;
+    const uint64_t c = g.base + V[jj];
     if (g.D && p - c > g.D) break;
     uint64_t lim = min64(p - c, seg_end - p);
     const uint64_t q0 = c >> g.log2_S, q1 = (c + lim - 1) >> g.log2_S;
@@ -121,6 +123,9 @@ ACE_HD uint64_t find_match(const ParseCtx &g, uint64_t s, uint32_t Ts, uint64_t 
       }
     }
     if (lim <= best) continue;
+    // a longer match than best agrees on bytes [0, best]: test the 8 bytes
+    // ending at best first (the outcome is the same, most losers cost one load)
+    if (best >= 7 && load_le64(g.in + c + best - 7) != load_le64(g.in + p + best - 7)) continue;
     const uint64_t L = common_len(g.in + c, g.in + p, lim);
     if (L > best) {
       best = L;
@@ -132,13 +137,44 @@ ACE_HD uint64_t find_match(const ParseCtx &g, uint64_t s, uint32_t Ts, uint64_t 
   return best;
 }
 
+// Match table of a window's positions (enc_match_kernel): t[p - p0] =
+// len << 32 | (p - src), 0 where the parse finds nothing; mask bit p - p0 is
+// set where the parse can use the match (length >= min_match, or any length
+// in sampled mode, where backward extension may lengthen it).
+struct TableFinder {
+  const uint64_t *t;
+  const uint64_t *mask;
+  uint64_t p0;
+  ACE_HD uint64_t operator()(uint64_t p, uint64_t *src) const {
+    const uint64_t v = t[p - p0];
+    const uint64_t len = v >> 32;
+    *src = len ? p - (uint32_t)v : 0;
+    return len;
+  }
+  // first position in [p, end) whose mask bit is set, else end
+  ACE_HD uint64_t next(uint64_t p, uint64_t end) const {
+    const uint64_t r = p - p0;
+    uint64_t w = r >> 6, bits = mask[w] & (~0ull << (r & 63));
+    while (!bits) {
+      ++w;
+      if (p0 + (w << 6) >= end) return end;
+      bits = mask[w];
+    }
+    const uint64_t q = p0 + (w << 6) + ctz64(bits);
+    return q < end ? q : end;
+  }
+};
+
 // Greedy parse of segment s with one-step lazy matching (content-defined
-// anchors with backward extension in sampled mode). Commands go to
+// anchors with backward extension in sampled mode); find(p, &src) gives the
+// match at p and find.next(p, end) skips the positions where the parse
+// can only emit a literal. Commands go to
 // lm[k] = lit_len | mlen << 16, srcs[k], dst[k] = destination - segment
 // start. Returns the command count; *overflow is set if cap_cmd would be
 // exceeded (the symbol budget makes that impossible).
-ACE_HD uint32_t parse_segment(const ParseCtx &g, uint64_t s, uint32_t *lm, uint64_t *srcs, uint16_t *dst,
-                              uint32_t cap_cmd, bool *overflow) {
+template <class Find>
+ACE_HD uint32_t parse_segment(const ParseCtx &g, uint64_t s, const Find &find, uint32_t *lm, uint64_t *srcs,
+                              uint16_t *dst, uint32_t cap_cmd, bool *overflow) {
   const uint64_t seg_start = s << g.log2_S, seg_end = min64(g.n, seg_start + g.S);
   const uint32_t Ts = ruler_target(s, g.cap);
   const uint64_t cs = 4 + g.W;
@@ -148,11 +184,15 @@ ACE_HD uint32_t parse_segment(const ParseCtx &g, uint64_t s, uint32_t *lm, uint6
   uint64_t next_len = 0, next_src = 0;
   const bool sparse = g.sample_mask != 0;
   while (p < seg_end) {
+    if (!have_next) {
+      p = find.next(p, seg_end);
+      if (p >= seg_end) break;
+    }
     const uint64_t p0 = p;
     uint64_t src = 0, len = 0;
     if (sparse) {
-      if (sampled(g, p)) {
-        len = find_match(g, s, Ts, p, seg_end, &src);
+      {
+        len = find(p, &src);
         if (len) {
           uint64_t back = 0;
           const uint64_t max_back = p - (src + len);
@@ -172,10 +212,10 @@ ACE_HD uint32_t parse_segment(const ParseCtx &g, uint64_t s, uint32_t *lm, uint6
       src = next_src;
       have_next = false;
     } else {
-      len = find_match(g, s, Ts, p, seg_end, &src);
+      len = find(p, &src);
     }
     if (!sparse && len >= g.min_match && p + 1 < seg_end) {
-      next_len = find_match(g, s, Ts, p + 1, seg_end, &next_src);
+      next_len = find(p + 1, &next_src);
       if (next_len > len) {
         len = 0;
         have_next = true;
@@ -275,7 +315,7 @@ ACE_HD uint32_t collect_deps(uint64_t s, uint32_t log2_S, uint32_t ncmd, const u
 // ------------------------------------------------------------ phase 1: chains
 
 __global__ void __launch_bounds__(256) enc_hash_kernel(const uint8_t *in, uint64_t base, uint64_t lim, uint32_t hlen,
-                                                       int bits, uint32_t sample_mask, uint32_t *hv, uint32_t *keys,
+                                                       int bits, uint32_t sample_mask, uint32_t *keys,
                                                        uint32_t *vals) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t ma = hlen >= 8 ? ~0ull : (1ull << (8 * hlen)) - 1;
@@ -285,17 +325,15 @@ __global__ void __launch_bounds__(256) enc_hash_kernel(const uint8_t *in, uint64
     const uint64_t a = load_le64(p) & ma;
     const uint64_t b = mb ? load_le64(p + 8) & mb : 0;
     const uint32_t h = hash_words(a, b, bits);
-    if (sample_mask) {
-      hv[i] = h;
-      keys[i] = (h & sample_mask) == 0 ? h : (1u << bits);  // unsampled positions sort last, unlinked
-    } else {
-      keys[i] = h;
-    }
+    // in sampled mode, unsampled positions get a key above every hash: they
+    // sort last and are nobody's candidate
+    keys[i] = (sample_mask && (h & sample_mask) != 0) ? (1u << bits) : h;
     vals[i] = (uint32_t)i;
   }
 }
 
 constexpr int kRsWarps = 8, kRsItems = 16, kRsTile = kRsWarps * 32 * kRsItems;  // 4096 pairs per tile
+constexpr int kRsSmem = 4 * kRsTile * 4;  // scatter: the tile in input order and in digit order (keys, values)
 
 __global__ void __launch_bounds__(256) rs_hist_kernel(const uint32_t *keys, uint64_t n, int shift, uint32_t ntiles,
                                                       uint32_t *hist) {
@@ -314,26 +352,36 @@ __global__ void __launch_bounds__(256) rs_hist_kernel(const uint32_t *keys, uint
 // Stable scatter of one tile: warp w owns pairs [tile + 512w, tile + 512w +
 // 512), visited in index order (item k of lane l is 32k + l); the rank of a
 // pair among equal digits is the count in earlier warps + earlier items of
-// its warp + earlier lanes of its item (match_any groups equal digits).
+// its warp + earlier lanes of its item (match_any groups equal digits). The
+// tile is first ordered by digit in shared memory, so that each digit's run
+// leaves as consecutive stores. The pairs wait in shared memory in input
+// order meanwhile (only their ranks stay in registers).
 __global__ void __launch_bounds__(256) rs_scatter_kernel(const uint32_t *kin, const uint32_t *vin, uint64_t n,
                                                          int shift, uint32_t ntiles, const uint32_t *offs,
                                                          uint32_t *kout, uint32_t *vout) {
-  __shared__ uint32_t toff[256];
+  extern __shared__ uint32_t rs_dyn[];
+  uint32_t *ink = rs_dyn, *inv = rs_dyn + kRsTile, *sk = rs_dyn + 2 * kRsTile, *sv = rs_dyn + 3 * kRsTile;
+  __shared__ uint32_t toff[256], tstart[256], wsum[kRsWarps];
   __shared__ uint32_t wc[kRsWarps][256];
   const uint32_t tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   toff[tid] = offs[(uint64_t)tid * ntiles + blockIdx.x];
   for (uint32_t j = tid; j < kRsWarps * 256; j += 256) (&wc[0][0])[j] = 0;
   __syncthreads();
-  const uint64_t wbase = (uint64_t)blockIdx.x * kRsTile + (uint64_t)w * 32 * kRsItems;
+  const uint64_t tbase = (uint64_t)blockIdx.x * kRsTile;
+  const uint64_t wbase = tbase + (uint64_t)w * 32 * kRsItems;
   const uint32_t lt = (1u << lane) - 1;
-  uint32_t key[kRsItems], val[kRsItems], rk[kRsItems];
+  const uint32_t lbase = w * 32 * kRsItems + lane;  // tile-local index of item 0
+  uint32_t rk[kRsItems];
 #pragma unroll
   for (int k = 0; k < kRsItems; ++k) {
     const uint64_t idx = wbase + (uint64_t)k * 32 + lane;
     const bool valid = idx < n;
-    key[k] = valid ? kin[idx] : 0;
-    val[k] = valid ? vin[idx] : 0;
-    const uint32_t d = valid ? (key[k] >> shift) & 255u : 256u;
+    const uint32_t key = valid ? kin[idx] : 0;
+    if (valid) {
+      ink[lbase + 32 * k] = key;
+      inv[lbase + 32 * k] = vin[idx];
+    }
+    const uint32_t d = valid ? (key >> shift) & 255u : 256u;
     const uint32_t peers = __match_any_sync(kFull, d);
     const uint32_t before = valid ? wc[w][d] : 0;
     __syncwarp();
@@ -342,35 +390,78 @@ __global__ void __launch_bounds__(256) rs_scatter_kernel(const uint32_t *kin, co
     rk[k] = before + __popc(peers & lt);
   }
   __syncthreads();
-  {
-    uint32_t run = 0;
-    for (int v = 0; v < kRsWarps; ++v) {
-      const uint32_t c = wc[v][tid];
-      wc[v][tid] = run;
-      run += c;
-    }
+  // thread tid = digit: per-warp prefix of its count, then the tile's
+  // exclusive prefix over digits (start of the digit's run in the tile)
+  uint32_t cnt = 0;
+  for (int v = 0; v < kRsWarps; ++v) {
+    const uint32_t c = wc[v][tid];
+    wc[v][tid] = cnt;
+    cnt += c;
   }
+  uint32_t inc = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, inc, o);
+    if (lane >= (uint32_t)o) inc += y;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  uint32_t wpre = 0;
+  for (uint32_t v = 0; v < w; ++v) wpre += wsum[v];
+  tstart[tid] = wpre + inc - cnt;
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < kRsItems; ++k) {
     const uint64_t idx = wbase + (uint64_t)k * 32 + lane;
     if (idx < n) {
-      const uint32_t d = (key[k] >> shift) & 255u;
-      const uint64_t dest = (uint64_t)toff[d] + wc[w][d] + rk[k];
-      kout[dest] = key[k];
-      vout[dest] = val[k];
+      const uint32_t key = ink[lbase + 32 * k], d = (key >> shift) & 255u;
+      const uint32_t at = tstart[d] + wc[w][d] + rk[k];
+      sk[at] = key;
+      sv[at] = inv[lbase + 32 * k];
     }
+  }
+  __syncthreads();
+  const uint32_t tile_n = (uint32_t)min64(kRsTile, n - tbase);
+  for (uint32_t i = tid; i < tile_n; i += 256) {
+    const uint32_t k = sk[i], d = (k >> shift) & 255u;
+    const uint64_t dest = (uint64_t)toff[d] + (i - tstart[d]);
+    kout[dest] = k;
+    vout[dest] = sv[i];
   }
 }
 
-__global__ void __launch_bounds__(256) enc_link_kernel(const uint32_t *K, const uint32_t *V, uint64_t m,
-                                                       uint32_t sentinel, uint32_t *prev) {
+// The match of every position of [a, b) that lies in the sorted window, one
+// thread per sorted slot: candidates are the preceding slots (coalesced
+// reads instead of a dependent walk), the result goes to t[p - a].
+__global__ void __launch_bounds__(256) enc_match_kernel(ParseCtx g, const uint32_t *K, const uint32_t *V, uint64_t m,
+                                                        uint32_t sentinel, uint64_t a, uint64_t b, uint64_t *table) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
-    const uint32_t k = K[j];
-    uint32_t pv = 0;
-    if (j > 0 && k != sentinel && K[j - 1] == k) pv = V[j - 1] + 1;
-    prev[V[j]] = pv;
+    const uint64_t p = g.base + V[j];
+    if (p < a || p >= b) continue;  // history before the window: a candidate only
+    uint64_t v = 0;
+    if (K[j] != sentinel) {
+      uint64_t src;
+      const uint64_t len = match_at_slot(g, K, V, j, p, &src);
+      if (len) v = (len << 32) | (p - src);
+    }
+    table[p - a] = v;
+  }
+}
+
+// One 64-bit mask word per warp iteration: bit q set when the match at
+// position q of the table is usable (length >= min_len).
+__global__ void __launch_bounds__(256) enc_mask_kernel(const uint64_t *table, uint64_t np, uint64_t min_len,
+                                                       uint64_t *mask) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t nwords = (np + 63) >> 6;
+  const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t w = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < nwords; w += nwarps) {
+    const uint64_t i0 = (w << 6) + lane, i1 = i0 + 32;
+    const bool b0 = i0 < np && (table[i0] >> 32) >= min_len;
+    const bool b1 = i1 < np && (table[i1] >> 32) >= min_len;
+    const uint32_t lo = __ballot_sync(kFull, b0), hi = __ballot_sync(kFull, b1);
+    if (lane == 0) mask[w] = (uint64_t)lo | ((uint64_t)hi << 32);
   }
 }
 
@@ -474,38 +565,47 @@ struct BatchBufs {
   uint32_t cap_cmd;
 };
 
-__global__ void __launch_bounds__(128) enc_parse_kernel(ParseCtx g, uint64_t s0, uint32_t nb, BatchBufs b,
-                                                        uint32_t *err) {
+__global__ void __launch_bounds__(128) enc_parse_kernel(ParseCtx g, uint64_t s0, uint32_t nb, TableFinder find,
+                                                        BatchBufs b, uint32_t *err) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
-  const uint64_t s = s0 + i, slot = (uint64_t)i * b.cap_cmd;
+  const uint64_t s = s0 + i, cmd0 = (uint64_t)i * b.cap_cmd;  // the segment's first command slot
   bool overflow = false;
-  const uint32_t nc = parse_segment(g, s, b.lm + slot, b.srcs + slot, b.dst + slot, b.cap_cmd, &overflow);
+  const uint32_t nc = parse_segment(g, s, find, b.lm + cmd0, b.srcs + cmd0, b.dst + cmd0, b.cap_cmd, &overflow);
   if (overflow) atomicOr(err, kErrCmdCap);
-  flatten(g, s << g.log2_S, nc, b.lm + slot, b.srcs + slot, b.dst + slot);
+  flatten(g, s << g.log2_S, nc, b.lm + cmd0, b.srcs + cmd0, b.dst + cmd0);
   b.ncmd[i] = nc;
-  b.ndep[i] = collect_deps(s, g.log2_S, nc, b.lm + slot, b.srcs + slot, b.deptmp + 2 * slot);
+  b.ndep[i] = collect_deps(s, g.log2_S, nc, b.lm + cmd0, b.srcs + cmd0, b.deptmp + 2 * cmd0);
 }
 
 // One warp per segment: the symbol message (FORMAT.md §3) into
-// sym[s * kMaxSym ...] and the per-class symbol counts.
+// sym[s * slot ...] and the per-class symbol counts.
 __global__ void __launch_bounds__(256) enc_symbols_kernel(const uint8_t *in, uint64_t n, uint64_t s0, uint32_t nb,
                                                           uint32_t log2_S, uint32_t W, uint32_t min_match,
-                                                          BatchBufs b, uint8_t *sym, uint32_t *n_cmd,
-                                                          uint32_t *n_lit, unsigned long long *counts) {
+                                                          BatchBufs b, uint8_t *sym, uint32_t slot,
+                                                          uint32_t *n_cmd, uint32_t *n_lit,
+                                                          unsigned long long *counts, uint32_t *err) {
   __shared__ uint32_t hist[1024];
   for (uint32_t j = threadIdx.x; j < 1024; j += blockDim.x) hist[j] = 0;
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t wpb = blockDim.x >> 5;
   for (uint32_t i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nb; i += gridDim.x * wpb) {
-    const uint64_t s = s0 + i, slot = (uint64_t)i * b.cap_cmd;
+    const uint64_t s = s0 + i, cmd0 = (uint64_t)i * b.cap_cmd;
     const uint32_t nc = b.ncmd[i];
-    const uint32_t *lm = b.lm + slot;
-    const uint64_t *srcs = b.srcs + slot;
-    uint8_t *out = sym + s * kMaxSym;
+    const uint32_t *lm = b.lm + cmd0;
+    const uint64_t *srcs = b.srcs + cmd0;
+    uint8_t *out = sym + s * slot;
     const uint64_t seg_start = s << log2_S;
     const uint64_t seg_len = min64(n - seg_start, uint64_t(1) << log2_S);
+    uint64_t mlen_sum = 0;  // the symbol count is n_cmd (4 + W) + seg_len - sum of match lengths
+    for (uint32_t k = lane; k < nc; k += 32) mlen_sum += lm[k] >> 16;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mlen_sum += __shfl_xor_sync(kFull, mlen_sum, o);
+    if ((uint64_t)(4 + W) * nc + seg_len - mlen_sum > slot) {  // cannot happen: the parse keeps n_sym <= slot
+      if (lane == 0) atomicOr(err, kErrSymbols);
+      continue;
+    }
     for (uint32_t k = lane; k < nc; k += 32) {
       const uint32_t v = lm[k], ll = v & 0xffffu, mv = (v >> 16) - min_match;
       out[2 * k] = (uint8_t)ll;
@@ -592,7 +692,7 @@ __global__ void __launch_bounds__(256) enc_deps_copy_kernel(uint64_t s0, uint32_
 // One warp per segment: the FORMAT.md §4 encoder, 32 lanes, symbols in
 // reverse order. Pass 1 (payload == nullptr) counts the words; pass 2
 // writes the 32 initial states and the words in decode order.
-__global__ void __launch_bounds__(256) enc_rans_kernel(const uint8_t *sym, const uint32_t *n_cmd,
+__global__ void __launch_bounds__(256) enc_rans_kernel(const uint8_t *sym, uint32_t slot, const uint32_t *n_cmd,
                                                        const uint32_t *n_lit, uint64_t n_seg, uint32_t W,
                                                        const uint16_t *tabs, uint32_t *n_words, uint8_t *payload,
                                                        const uint64_t *poff) {
@@ -608,7 +708,7 @@ __global__ void __launch_bounds__(256) enc_rans_kernel(const uint8_t *sym, const
     const uint32_t nc = n_cmd[s];
     const uint32_t ns = nc * (4 + W) + n_lit[s];
     const uint32_t b1 = 2 * nc, b2 = 4 * nc, b3 = (4 + W) * nc;
-    const uint8_t *m = sym + s * kMaxSym;
+    const uint8_t *m = sym + s * slot;
     uint32_t x = kRansL;
     uint32_t tail = payload ? n_words[s] : 0, count = 0;
     uint8_t *wbase = payload ? payload + poff[s] + 128 : nullptr;
@@ -709,13 +809,13 @@ struct aceapex_gpu_encoder {
   cudaStream_t st = nullptr;
   cudaEvent_t ev[6] = {};
   uint64_t launches = 0;  // kernels launched by the current call
-  aceapex::Buf in, hv, kA, vA, kB, vB, prev, hist, part, scan_tmp;
-  aceapex::Buf lm, srcs, dst, deptmp, bncmd, bndep;
+  aceapex::Buf in, kA, vA, kB, vB, hist, part;
+  aceapex::Buf lm, srcs, dst, deptmp, bncmd, bndep, mtab, mask;
   aceapex::Buf sym, n_cmd, n_lit, n_words, level, dep_ptr, deps, poff, sz;
   aceapex::Buf counts, tabs, err, arc;
   ~aceapex_gpu_encoder() {
-    aceapex::Buf *all[] = {&in, &hv, &kA, &vA, &kB, &vB, &prev, &hist, &part, &scan_tmp, &lm, &srcs, &dst,
-                           &deptmp, &bncmd, &bndep, &sym, &n_cmd, &n_lit, &n_words, &level, &dep_ptr, &deps,
+    aceapex::Buf *all[] = {&in, &kA, &vA, &kB, &vB, &hist, &part, &lm, &srcs, &dst,
+                           &deptmp, &bncmd, &bndep, &mtab, &mask, &sym, &n_cmd, &n_lit, &n_words, &level, &dep_ptr, &deps,
                            &poff, &sz, &counts, &tabs, &err, &arc};
     for (auto *b : all) b->release();
     for (auto &e : ev)
@@ -750,24 +850,25 @@ int device_scan(aceapex_gpu_encoder *E, const Tin *in, uint64_t n, Tout *out, co
   return cuda_rc(cudaGetLastError());
 }
 
-// Phase 1 for the window [base, end): prev links of every position.
-int build_chains(aceapex_gpu_encoder *E, uint64_t n, uint64_t base, uint64_t end, uint32_t hlen, uint32_t smask,
-                 uint64_t *lim_out) {
+// Phase 1 for the window [base, end): the hashed positions [base, base +
+// lim) sorted stably by hash; *K, *V receive the sorted keys and positions
+// (relative to base).
+int sort_window(aceapex_gpu_encoder *E, uint64_t n, uint64_t base, uint64_t end, uint32_t hlen, uint32_t smask,
+                uint64_t *lim_out, const uint32_t **K, const uint32_t **V, uint32_t *sentinel) {
   const uint64_t len = end - base;
   const int bits = hash_bits_for(len);
   const uint64_t lim = (base + hlen <= n) ? std::min<uint64_t>(len, n - hlen + 1 - base) : 0;
   *lim_out = lim;
-  ENC_TRY(E->prev.reserve(4 * std::max<uint64_t>(len, 1)));
-  ENC_TRY(cudaMemsetAsync(E->prev.p, 0, 4 * len, E->st));
+  *sentinel = smask ? (1u << bits) : 0xffffffffu;
+  *K = *V = nullptr;
   if (lim == 0) return ACEAPEX_OK;
   ENC_TRY(E->kA.reserve(4 * lim));
   ENC_TRY(E->vA.reserve(4 * lim));
   ENC_TRY(E->kB.reserve(4 * lim));
   ENC_TRY(E->vB.reserve(4 * lim));
-  if (smask) ENC_TRY(E->hv.reserve(4 * lim));
   const unsigned grid = (unsigned)E->sms * 8;
-  enc_hash_kernel<<<grid, 256, 0, E->st>>>(E->in.as<uint8_t>(), base, lim, hlen, bits, smask, E->hv.as<uint32_t>(),
-                                          E->kA.as<uint32_t>(), E->vA.as<uint32_t>());
+  enc_hash_kernel<<<grid, 256, 0, E->st>>>(E->in.as<uint8_t>(), base, lim, hlen, bits, smask, E->kA.as<uint32_t>(),
+                                          E->vA.as<uint32_t>());
   ++E->launches;
   ENC_TRY(cudaGetLastError());
   const int key_bits = bits + (smask ? 1 : 0);
@@ -782,17 +883,16 @@ int build_chains(aceapex_gpu_encoder *E, uint64_t n, uint64_t base, uint64_t end
     const int rc = device_scan<uint32_t, uint32_t>(E, E->hist.as<uint32_t>(), 256 * ntiles, E->hist.as<uint32_t>(),
                                                    nullptr, false);
     if (rc) return rc;
-    rs_scatter_kernel<<<(unsigned)ntiles, 256, 0, E->st>>>(ki, vi, lim, shift, (uint32_t)ntiles,
-                                                          E->hist.as<uint32_t>(), ko, vo);
+    rs_scatter_kernel<<<(unsigned)ntiles, 256, kRsSmem, E->st>>>(ki, vi, lim, shift, (uint32_t)ntiles,
+                                                                E->hist.as<uint32_t>(), ko, vo);
     ++E->launches;
     ENC_TRY(cudaGetLastError());
     std::swap(ki, ko);
     std::swap(vi, vo);
   }
-  const uint32_t sentinel = smask ? (1u << bits) : 0xffffffffu;
-  enc_link_kernel<<<grid, 256, 0, E->st>>>(ki, vi, lim, sentinel, E->prev.as<uint32_t>());
-  ++E->launches;
-  return cuda_rc(cudaGetLastError());
+  *K = ki;
+  *V = vi;
+  return ACEAPEX_OK;
 }
 
 inline void put32(uint8_t *p, uint32_t v) { std::memcpy(p, &v, 4); }
@@ -817,7 +917,11 @@ int gpu_encode(aceapex_gpu_encoder *E, const uint8_t *in, int in_on_device, uint
   cudaStream_t st = E->st;
   E->launches = 0;
   const uint32_t hlen = hash_len_for(mm), smask = sample_mask_for(mm);
-  const uint32_t cap_cmd = kMaxSym / (4 + W) + 1;
+  // a segment has at most S commands (every match is at least one byte) and
+  // kMaxSym / (4 + W) of them (rule R-sym); its symbols number at most
+  // kMaxSym and at most (4 + W) per byte
+  const uint32_t cap_cmd = (uint32_t)std::min<uint64_t>(kMaxSym / (4 + W) + 1, S);
+  const uint32_t slot = (uint32_t)std::min<uint64_t>(kMaxSym, S * (4 + W));
 
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> chain_ev, parse_ev, match_ev;
   auto fresh_event = [](cudaEvent_t *e) { return cudaEventCreate(e); };
@@ -843,7 +947,7 @@ int gpu_encode(aceapex_gpu_encoder *E, const uint8_t *in, int in_on_device, uint
   ENC_TRY(E->counts.reserve(8 * 1024));
   ENC_TRY(cudaMemsetAsync(E->counts.p, 0, 8 * 1024, st));
   const uint64_t segs = std::max<uint64_t>(n_seg, 1);
-  ENC_TRY(E->sym.reserve(segs * kMaxSym));
+  ENC_TRY(E->sym.reserve(segs * slot));
   ENC_TRY(E->n_cmd.reserve(4 * segs));
   ENC_TRY(E->n_lit.reserve(4 * segs));
   ENC_TRY(E->n_words.reserve(4 * segs));
@@ -860,12 +964,14 @@ int gpu_encode(aceapex_gpu_encoder *E, const uint8_t *in, int in_on_device, uint
   ENC_TRY(E->deptmp.reserve(8ull * batch * cap_cmd));
   ENC_TRY(E->bncmd.reserve(4ull * batch));
   ENC_TRY(E->bndep.reserve(4ull * batch));
+  const uint64_t chunk = D ? std::max<uint64_t>(kDistWindow, S) : std::max<uint64_t>(n, 1);
+  ENC_TRY(E->mtab.reserve(8 * std::min<uint64_t>(chunk, std::max<uint64_t>(n, 1))));
+  ENC_TRY(E->mask.reserve(8 * ((std::min<uint64_t>(chunk, std::max<uint64_t>(n, 1)) + 63) / 64)));
   BatchBufs bb{E->lm.as<uint32_t>(), E->srcs.as<uint64_t>(), E->dst.as<uint16_t>(), E->deptmp.as<uint32_t>(),
                E->bncmd.as<uint32_t>(), E->bndep.as<uint32_t>(), cap_cmd};
   uint64_t deps_used = 0;  // entries of deps written so far
 
   // ---- phases 1-3, window by window (the host encoder's windows)
-  const uint64_t chunk = D ? std::max<uint64_t>(kDistWindow, S) : std::max<uint64_t>(n, 1);
   for (uint64_t a = 0; a < n; a += chunk) {
     const uint64_t b = std::min(n, a + chunk);
     const uint64_t base = D ? (a > D ? a - D : 0) : 0;
@@ -874,29 +980,44 @@ int gpu_encode(aceapex_gpu_encoder *E, const uint8_t *in, int in_on_device, uint
     ENC_TRY(fresh_event(&chain_ev.back().second));
     ENC_TRY(cudaEventRecord(chain_ev.back().first, st));
     uint64_t lim = 0;
-    int rc = build_chains(E, n, base, b, hlen, smask, &lim);
+    const uint32_t *K = nullptr, *V = nullptr;
+    uint32_t sentinel = 0;
+    int rc = sort_window(E, n, base, b, hlen, smask, &lim, &K, &V, &sentinel);
     if (rc) return rc;
     ENC_TRY(cudaEventRecord(chain_ev.back().second, st));
+    // match table of [a, b) and its mask; positions past the last full hash
+    // window have no match
+    const ParseCtx g{E->in.as<uint8_t>(), n, base, S, D, log2_S, W, mm, cap, smask};
+    uint64_t *table = E->mtab.as<uint64_t>();
+    const uint64_t hashed_end = std::max(a, std::min(b, base + lim));
+    if (hashed_end < b) ENC_TRY(cudaMemsetAsync(table + (hashed_end - a), 0, 8 * (b - hashed_end), st));
+    match_ev.emplace_back(nullptr, nullptr);
+    ENC_TRY(fresh_event(&match_ev.back().first));
+    ENC_TRY(fresh_event(&match_ev.back().second));
+    ENC_TRY(cudaEventRecord(match_ev.back().first, st));
+    if (lim) {
+      enc_match_kernel<<<(unsigned)E->sms * 16, 256, 0, st>>>(g, K, V, lim, sentinel, a, b, table);
+      ++E->launches;
+      ENC_TRY(cudaGetLastError());
+    }
+    ENC_TRY(cudaEventRecord(match_ev.back().second, st));
     parse_ev.emplace_back(nullptr, nullptr);
     ENC_TRY(fresh_event(&parse_ev.back().first));
     ENC_TRY(fresh_event(&parse_ev.back().second));
     ENC_TRY(cudaEventRecord(parse_ev.back().first, st));
-    ParseCtx g{E->in.as<uint8_t>(), n, E->prev.as<uint32_t>(), E->hv.as<uint32_t>(), base, lim, S, D,
-               log2_S, W, mm, cap, hlen, smask};
+    enc_mask_kernel<<<(unsigned)E->sms * 8, 256, 0, st>>>(table, b - a, smask ? 1 : mm, E->mask.as<uint64_t>());
+    ++E->launches;
+    ENC_TRY(cudaGetLastError());
+    const TableFinder find{table, E->mask.as<uint64_t>(), a};
     const uint64_t s_lo = a >> log2_S, s_hi = (b + S - 1) >> log2_S;
     for (uint64_t s0 = s_lo; s0 < s_hi; s0 += batch) {
       const uint32_t nb = (uint32_t)std::min<uint64_t>(batch, s_hi - s0);
-      match_ev.emplace_back(nullptr, nullptr);
-      ENC_TRY(fresh_event(&match_ev.back().first));
-      ENC_TRY(fresh_event(&match_ev.back().second));
-      ENC_TRY(cudaEventRecord(match_ev.back().first, st));
-      enc_parse_kernel<<<(nb + 127) / 128, 128, 0, st>>>(g, s0, nb, bb, E->err.as<uint32_t>());
+      enc_parse_kernel<<<(nb + 127) / 128, 128, 0, st>>>(g, s0, nb, find, bb, E->err.as<uint32_t>());
       ++E->launches;
       ENC_TRY(cudaGetLastError());
-      ENC_TRY(cudaEventRecord(match_ev.back().second, st));
       enc_symbols_kernel<<<(unsigned)E->sms * 8, 256, 0, st>>>(
-          E->in.as<uint8_t>(), n, s0, nb, log2_S, W, mm, bb, E->sym.as<uint8_t>(), E->n_cmd.as<uint32_t>(),
-          E->n_lit.as<uint32_t>(), E->counts.as<unsigned long long>());
+          E->in.as<uint8_t>(), n, s0, nb, log2_S, W, mm, bb, E->sym.as<uint8_t>(), slot, E->n_cmd.as<uint32_t>(),
+          E->n_lit.as<uint32_t>(), E->counts.as<unsigned long long>(), E->err.as<uint32_t>());
       ++E->launches;
       ENC_TRY(cudaGetLastError());
       for (uint32_t tier = 0; tier <= cap; ++tier) {
@@ -942,7 +1063,7 @@ int gpu_encode(aceapex_gpu_encoder *E, const uint8_t *in, int in_on_device, uint
   const unsigned rgrid = (unsigned)E->sms * 8;
   uint64_t payload = 0;
   if (n_seg) {
-    enc_rans_kernel<<<rgrid, 256, 0, st>>>(E->sym.as<uint8_t>(), E->n_cmd.as<uint32_t>(), E->n_lit.as<uint32_t>(),
+    enc_rans_kernel<<<rgrid, 256, 0, st>>>(E->sym.as<uint8_t>(), slot, E->n_cmd.as<uint32_t>(), E->n_lit.as<uint32_t>(),
                                           n_seg, W, E->tabs.as<uint16_t>(), E->n_words.as<uint32_t>(), nullptr,
                                           nullptr);
     ENC_TRY(cudaGetLastError());
@@ -1005,7 +1126,7 @@ int gpu_encode(aceapex_gpu_encoder *E, const uint8_t *in, int in_on_device, uint
   if (n_deps) ENC_TRY(cudaMemcpyAsync(A + off_deps, E->deps.p, 4 * n_deps, cudaMemcpyDeviceToDevice, st));
   if (n_reads) ENC_TRY(cudaMemcpyAsync(A + off_reads, reads, 8 * n_reads, cudaMemcpyHostToDevice, st));
   if (n_seg) {
-    enc_rans_kernel<<<rgrid, 256, 0, st>>>(E->sym.as<uint8_t>(), E->n_cmd.as<uint32_t>(), E->n_lit.as<uint32_t>(),
+    enc_rans_kernel<<<rgrid, 256, 0, st>>>(E->sym.as<uint8_t>(), slot, E->n_cmd.as<uint32_t>(), E->n_lit.as<uint32_t>(),
                                           n_seg, W, E->tabs.as<uint16_t>(), E->n_words.as<uint32_t>(),
                                           A + off_payload, E->poff.as<uint64_t>());
     ++E->launches;
@@ -1033,15 +1154,14 @@ int gpu_encode(aceapex_gpu_encoder *E, const uint8_t *in, int in_on_device, uint
       cudaEventElapsedTime(&ms, pr.first, pr.second);
       stats->ms_chains += ms;
     }
+    for (auto &pr : match_ev) {
+      cudaEventElapsedTime(&ms, pr.first, pr.second);
+      stats->ms_match += ms;
+    }
     for (auto &pr : parse_ev) {
       cudaEventElapsedTime(&ms, pr.first, pr.second);
       stats->ms_parse += ms;
     }
-    for (auto &pr : match_ev) {
-      cudaEventElapsedTime(&ms, pr.first, pr.second);
-      stats->ms_parse_kernel += ms;
-    }
-    stats->parse_launches = match_ev.size();
     stats->kernel_launches = E->launches;
     cudaEventElapsedTime(&ms, parse_ev.empty() ? E->ev[1] : parse_ev.back().second, E->ev[2]);
     stats->ms_entropy = ms;
@@ -1076,6 +1196,8 @@ int aceapex_gpu_encoder_create(int device, aceapex_gpu_encoder **out) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&E->st, cudaStreamNonBlocking);
   for (auto &ev : E->ev)
     if (e == cudaSuccess) e = cudaEventCreate(&ev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(aceapex::rs_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, aceapex::kRsSmem);
   if (e != cudaSuccess) {
     delete E;
     return ACEAPEX_ECUDA;

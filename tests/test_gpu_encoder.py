@@ -2,8 +2,9 @@
 archive must equal the host encoder's byte for byte, and the oracle must
 decode it (validating every rule of the format on the way) back to the input.
 The GPU decoder reads it back too. Inputs span the radix sort's tiles and
-ragged tails, several segment batches, sampled and full hashing, a distance
-bound, small segments, min_match 1, and the degenerate sizes."""
+ragged tails, several parse batches (4-byte segments), sampled and full
+hashing, a distance bound, small segments, min_match 1, and the degenerate
+sizes."""
 import numpy as np
 import pytest
 
@@ -52,6 +53,8 @@ CASES = [
     ("tiny", dict(log2_B=10, min_match=6), False),
     ("tiny", dict(min_match=1), False),
     ("tiny", dict(log2_B=20, min_match=16, max_level=0), False),
+    ("tiny", dict(log2_B=2, min_match=3), False),
+    ("tiny", dict(log2_B=6, min_match=3, dist_bound=7), False),
     ("fasta", dict(min_match=32, dist_bound=1 << 20), False),
     ("fasta", dict(min_match=12), False),
     ("pe", dict(min_match=16), True),
