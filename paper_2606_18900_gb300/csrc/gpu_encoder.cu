@@ -898,9 +898,9 @@ int sort_window(aceapex_gpu_encoder *E, uint64_t n, uint64_t base, uint64_t end,
 inline void put32(uint8_t *p, uint32_t v) { std::memcpy(p, &v, 4); }
 inline void put64(uint8_t *p, uint64_t v) { std::memcpy(p, &v, 8); }
 
-int gpu_encode(aceapex_gpu_encoder *E, const uint8_t *in, int in_on_device, uint64_t n, uint32_t log2_B,
-               uint32_t min_match, uint32_t cap, uint64_t D, const uint64_t *reads, uint64_t n_reads, uint8_t **out,
-               uint64_t *out_len, aceapex_encode_stats *stats) {
+int gpu_encode_steps(aceapex_gpu_encoder *E, const uint8_t *in, int in_on_device, uint64_t n, uint32_t log2_B,
+                     uint32_t min_match, uint32_t cap, uint64_t D, const uint64_t *reads, uint64_t n_reads,
+                     uint8_t **out, uint64_t *out_len, aceapex_encode_stats *stats) {
   if (log2_B < 2 || log2_B > 30 || cap > 255 || (n && !in) || !out || !out_len || (n_reads && !reads))
     return ACEAPEX_EINVAL;
   const uint32_t log2_S = std::min<uint32_t>(log2_B, kMaxLog2S);
@@ -1176,6 +1176,18 @@ int gpu_encode(aceapex_gpu_encoder *E, const uint8_t *in, int in_on_device, uint
     stats->windows = chain_ev.size();
   }
   return ACEAPEX_OK;
+}
+
+// A call that fails part-way waits for the kernels it already queued, so
+// that none is still running when the caller frees or reuses memory, or
+// exits.
+int gpu_encode(aceapex_gpu_encoder *E, const uint8_t *in, int in_on_device, uint64_t n, uint32_t log2_B,
+               uint32_t min_match, uint32_t cap, uint64_t D, const uint64_t *reads, uint64_t n_reads, uint8_t **out,
+               uint64_t *out_len, aceapex_encode_stats *stats) {
+  const int rc =
+      gpu_encode_steps(E, in, in_on_device, n, log2_B, min_match, cap, D, reads, n_reads, out, out_len, stats);
+  if (rc != ACEAPEX_OK && E->st) cudaStreamSynchronize(E->st);
+  return rc;
 }
 
 }  // namespace

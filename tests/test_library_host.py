@@ -132,6 +132,15 @@ def test_fastq_split_streams():
         assert sum(s.size for s in streams) == x.size
 
 
+def test_gpu_encoder_fails_loudly_without_a_device():
+    """No CPU fallback: without a CUDA device the GPU encoder cannot be made."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present (covered by the GPU tests)")
+    with pytest.raises(ace.AceapexError):
+        ace.GpuEncoder(0)
+
+
 def test_empty_input():
     a = ace.encode(np.zeros(0, np.uint8))
     assert oracle.decode(a).size == 0
