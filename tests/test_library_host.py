@@ -132,6 +132,48 @@ def test_fastq_split_streams():
         assert sum(s.size for s in streams) == x.size
 
 
+@pytest.fixture(scope="module")
+def encoder_emulation(tmp_path_factory):
+    """tests/support/encoder_emulation.cu built for the host (nvcc)."""
+    import shutil
+    import subprocess
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    csrc = os.path.join(ROOT, "paper_2606_18900_gb300", "csrc")
+    exe = str(tmp_path_factory.mktemp("emul") / "encoder_emulation")
+    r = subprocess.run([nvcc, "-O2", "-std=c++17", "-I" + csrc, "-I" + os.path.join(ROOT, "include"),
+                        "-gencode", "arch=compute_103a,code=sm_103a",
+                        os.path.join(ROOT, "tests", "support", "encoder_emulation.cu"),
+                        os.path.join(csrc, "encoder.cpp"), "-o", exe, "-lpthread"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return exe
+
+
+@pytest.mark.parametrize("make,cases", [
+    ("tiny", ["14,16,8,0", "14,0,8,0", "12,8,3,0", "14,40,8,0", "14,16,8,5000", "10,6,8,0", "14,1,8,0",
+              "2,3,8,0", "6,3,8,7", "20,16,0,0"]),
+    ("fasta", ["14,32,8,1048576", "14,12,8,0"]),
+    ("random", ["14,0,8,0"]),
+    ("runs", ["14,0,8,0", "14,4,2,0"]),
+])
+def test_gpu_encoder_logic_equals_cpu_encoder(encoder_emulation, tmp_path, make, cases):
+    """The GPU encoder's match search, parse, flattening and dependency lists
+    (its __host__ __device__ functions, run on the host over a stable sort)
+    give the CPU encoder's archive byte for byte: sampled and full hashing,
+    distance bounds, 4-byte to 1 MiB blocks, level caps 0-8, min_match 1."""
+    import subprocess
+    data = {"tiny": lambda: synth.tiny_fastq(),
+            "fasta": lambda: synth.fasta(3_000_000, seed=41),
+            "random": lambda: synth.random_bytes(43, 1, 300_001),
+            "runs": lambda: np.full(200_003, ord("A"), dtype=np.uint8)}[make]()
+    f = tmp_path / "in.bin"
+    data.tofile(f)
+    r = subprocess.run([encoder_emulation, str(f)] + cases, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.count("same") == len(cases)
+
+
 def test_gpu_encoder_fails_loudly_without_a_device():
     """No CPU fallback: without a CUDA device the GPU encoder cannot be made."""
     torch = pytest.importorskip("torch")
