@@ -1,7 +1,7 @@
 // GPU encoder of the library: the match search of paper §2 (global search
 // over the whole decompressed history, absolute offsets, fixed-size blocks)
 // run on the device. The paper's encoder is CPU-only and names its speed as
-// the pipeline's bottleneck (§8, future work). This one applies the rules of
+// the pipeline's bottleneck (§8, Limitations). This one applies the rules of
 // the host encoder (encoder_rules.h) and writes the same archive, byte for
 // byte, in four phases:
 //
@@ -15,10 +15,10 @@
 //     dependent walk; a candidate whose 8 bytes ending at the current best
 //     length differ cannot win and is not compared further) into a table
 //     indexed by position, with a bitmask of the usable ones; then one
-//     thread per segment (the ruler level schedule
-//     makes segments independent) parses greedily with one-step lazy
-//     matching, jumping between mask bits, applies the symbol budget,
-//     flattens intra-segment chains and lists the segment's source segments.
+//     thread per segment (the ruler level schedule makes segments
+//     independent) parses greedily with one-step lazy matching, jumping
+//     between mask bits, applies the symbol budget, flattens intra-segment
+//     chains and lists the segment's source segments.
 //  3. symbols: one warp per segment writes the segment's symbol message
 //     (FORMAT.md §3) and counts symbols per class; levels follow tier by tier
 //     of the schedule (a segment only reads lower tiers); dependency lists
