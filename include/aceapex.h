@@ -341,10 +341,13 @@ int aceapex_decode_fastq_streams(aceapex_archive *const *parts, void *d_out, uin
  * tables) and returns the same archive, byte for byte.
  *
  * aceapex_gpu_encoder_create binds an encoder to a device; it owns a CUDA
- * stream and device scratch that grows on demand and is kept between calls
- * (16 bytes per position of a chain window, 8 per position of a parse window,
- * 16 KiB of symbols per segment, the archive). aceapex_gpu_encoder_destroy frees it all. Errors: EINVAL,
- * ENOMEM, ECUDA.
+ * stream and device scratch that grows on demand and is kept between calls:
+ * the input, 16 bytes per position of a chain window (sort keys and values,
+ * twice), 8 per position of a parse window (match table), up to 16 KiB of
+ * symbols per segment, and the archive; a 1 GiB input takes about 30 GB.
+ * aceapex_gpu_encoder_destroy frees it all. Calls on one encoder must be
+ * serialised by the caller (one scratch set); separate encoders are
+ * independent. Errors: EINVAL, ENOMEM, ECUDA.
  */
 typedef struct aceapex_gpu_encoder aceapex_gpu_encoder;
 
