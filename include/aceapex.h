@@ -2,7 +2,8 @@
  * aceapex.h — C ABI of libaceapex.so, a GB300 (sm_103a) decoder for the
  * absolute-offset LZ77 block format of "Compressed-Resident Genomics:
  * Full-Pipeline Device-Resident GPU LZ77 Decode with Position-Invariant
- * Random Access" (arXiv 2606.18900). The byte format is frozen in FORMAT.md.
+ * Random Access" (arXiv 2606.18900). The byte format is version 1 of the
+ * ACEAPEX1 archive format.
  *
  * Conventions
  *  - Every function returns an aceapex_status (0 = ACEAPEX_OK) unless noted.
@@ -32,7 +33,7 @@ extern "C" {
 typedef enum {
   ACEAPEX_OK = 0,
   ACEAPEX_EINVAL = 1,   /* bad argument */
-  ACEAPEX_ECORRUPT = 2, /* archive breaks a rule of FORMAT.md */
+  ACEAPEX_ECORRUPT = 2, /* archive breaks a rule of the format */
   ACEAPEX_ENOMEM = 3,   /* host or device allocation failed, or over budget */
   ACEAPEX_ECUDA = 4,    /* a CUDA runtime call failed */
   ACEAPEX_ETIMEOUT = 5, /* a dependency wait ran past its time limit */
@@ -58,7 +59,8 @@ typedef struct {
 } aceapex_stats;
 
 /*
- * Open an archive: validate it on the host (FORMAT.md §6) and copy the
+ * Open an archive: validate it on the host (header, tables, directory,
+ * dependency lists and read index against the format's rules) and copy the
  * sections the decoder needs into device memory on `device` (paper §3.3:
  * the archive is resident in VRAM before decoding; the copy is outside any
  * decode timer). The host bytes are not retained. On success *out owns the
@@ -80,7 +82,7 @@ int aceapex_get_stats(const aceapex_archive *a, aceapex_stats *st);
 
 /*
  * Histogram of the segments' dependency levels (the wavefront depth of paper
- * §2's block DAG under the level cap of FORMAT.md §2): h_counts[l] = number of
+ * §2's block DAG under the archive's level cap): h_counts[l] = number of
  * segments at level l, for l < n (levels >= n are not counted). Host only, no
  * GPU work. Errors: EINVAL (NULL pointers).
  */
@@ -236,7 +238,7 @@ int aceapex_server_get_stats(aceapex_server *s, aceapex_server_stats *out);
  * real-time pipeline that only allows allocation during initialisation. It
  * calls no cudaMalloc, cudaFree or allocating library routine.
  *
- * d_archive: the complete archive (FORMAT.md v1) in device memory, 16-byte
+ * d_archive: the complete archive (version 1) in device memory, 16-byte
  * aligned, nbytes long (caller-owned, read only). d_out: out_cap bytes of
  * device memory that receive the decoded output. d_status: one device word
  * that receives 0 or the aceapex_status of a device-side error once the work
@@ -260,7 +262,7 @@ int aceapex_decode_all_noalloc(const void *d_archive, uint64_t nbytes, void *d_o
 
 /*
  * Host encoder (paper §2: global match search, absolute offsets, fixed
- * blocks; the paper's encoder is CPU-only too). Produces a FORMAT.md v1
+ * blocks; the paper's encoder is CPU-only too). Produces a version-1
  * archive of h_in[0..n) in a malloc'd buffer *h_out (*out_len bytes; free
  * with aceapex_free). log2_B: block size exponent (2..30); min_match: 0 =
  * 4 + W; max_level: level cap; dist_bound: 0 = unbounded; h_reads /
@@ -369,7 +371,7 @@ void aceapex_gpu_encoder_destroy(aceapex_gpu_encoder *enc);
 
 /*
  * Encode in[0..n) (host memory, or device memory of the encoder's device when
- * in_on_device != 0) into a FORMAT.md v1 archive returned in a malloc'd host
+ * in_on_device != 0) into a version-1 archive returned in a malloc'd host
  * buffer *h_out of *out_len bytes (free with aceapex_free). Parameters and
  * their limits are those of aceapex_encode (n < 2^32 when dist_bound = 0,
  * dist_bound < 2^31). Synchronous: returns when the archive is in host

@@ -1,14 +1,14 @@
 """ACEAPEX CPU oracle — TEST INFRASTRUCTURE ONLY.
 
 Python access to ``oracle.c``: a plain, sequential encoder and decoder of the
-archive format in FORMAT.md, written from the paper's §2 (absolute offsets,
+archive format, written from the paper's §2 (absolute offsets,
 global match search, fixed blocks, four streams), §4.1 (read-to-block index)
 and §5 (64-bit fields, range decode). Only the tests, the package smoke
 check and the benchmark's CPU-baseline leg may import this package; the GPU
 library neither imports it nor shares code with it.
 
 Pins (tests/test_oracle_*.py): round trip on random, structured and
-adversarial inputs; a hand-derived worked example (FORMAT.md §7); brute-force
+adversarial inputs; a hand-derived worked example (tests/golden/abab_archive.txt); brute-force
 enumeration of every legal command list on tiny inputs; the rANS final-state
 invariant and the zero-order entropy bound; CRC-32 against zlib; the paper's
 printed block and index arithmetic (§4.1, §5); record starts by brute force.
@@ -147,7 +147,7 @@ def parse(data, log2_B: int = 14, min_match: int = 8, max_level: int = 8, D: int
 
 def serialize(data, cmds: np.ndarray, cmd_ptr: np.ndarray, log2_B: int = 14, min_match: int = 8,
               max_level: int = 8, D: int = 0, reads=None) -> np.ndarray:
-    """Archive from explicit commands (FORMAT.md §3-§5)."""
+    """Archive from explicit commands (the format's symbol message, rANS coding and layout)."""
     lib = _load()
     buf = _buf(data)
     cmds = np.ascontiguousarray(cmds, dtype=CMD_DTYPE)
@@ -289,7 +289,7 @@ def fastq_record_starts(data) -> np.ndarray:
 # ------------------------------------------------------- archive section views
 
 def sections(arc) -> dict:
-    """Raw header fields and section arrays of an archive (FORMAT.md §5)."""
+    """Raw header fields and section arrays of an archive (the format's section layout)."""
     a = _buf(arc)
     h = a[:128].tobytes()
     u64 = lambda o: int.from_bytes(h[o:o + 8], "little")

@@ -4,7 +4,7 @@
  * A plain, slow, sequential implementation of the absolute-offset LZ77 block
  * codec of the paper (§2: absolute back-references into the decompressed
  * output, global match search, fixed-size blocks, four streams per block; §5:
- * 64-bit size and offset fields) in the byte format frozen in FORMAT.md v1.
+ * 64-bit size and offset fields) in the byte format of version 1 of the archive format.
  * It exists to produce archives for the tests and to define the expected
  * decoded bytes. Only the tests, the package smoke check and the benchmark's
  * CPU-baseline leg may load it; the GPU library never links or calls it, and
@@ -13,14 +13,15 @@
  * Contents:
  *   orc_crc32            CRC-32/IEEE (reflected 0xEDB88320): the bitwise
  *                        definition and its byte-table form.
- *   orc_geometry         segment/block counts and offset width (FORMAT.md §1).
- *   orc_normalize        rANS frequency normalisation (FORMAT.md §4, tables).
+ *   orc_geometry         segment/block counts and offset width (segment geometry of the format).
+ *   orc_normalize        rANS frequency normalisation (the format's frequency
+ *                        tables: 256 u16 per class summing to 4096).
  *   orc_parse            encoder, match search (paper §2: global search over
  *                        the whole history, absolute offsets, fixed blocks),
  *                        greedy with one-step lazy evaluation, under the
  *                        level cap and distance bound readings.
- *   orc_serialize        streams + rANS + archive layout (FORMAT.md §3-§5).
- *   orc_decode           sequential decoder + validator (FORMAT.md §2-§6).
+ *   orc_serialize        streams + rANS + archive layout (the format's symbol message, rANS coding and layout).
+ *   orc_decode           sequential decoder + validator (every rule of the format).
  *   orc_decode_stream    the same decoder writing into a ring with one CRC
  *                        per window (paper §5 range decode; CRC replaces the
  *                        paper's FNV/XXH3 check).
@@ -103,7 +104,7 @@ static uint64_t get_u64(const uint8_t *p) {
   return v;
 }
 
-/* smallest w >= 1 with 256^w >= n (FORMAT.md §1) */
+/* smallest w >= 1 with 256^w >= n (segment geometry of the format) */
 static uint32_t offset_width(uint64_t n) {
   uint32_t w = 1;
   while (w < 8 && (n > (((uint64_t)1) << (8 * w)))) ++w;
@@ -169,7 +170,7 @@ static int make_geom(uint64_t n, uint32_t log2_B, uint32_t min_match, uint32_t m
   return ORC_OK;
 }
 
-/* n_segments, n_blocks and W of an archive of n bytes (FORMAT.md §1) */
+/* n_segments, n_blocks and W of an archive of n bytes (segment geometry of the format) */
 int orc_geometry(uint64_t n, uint32_t log2_B, uint64_t *n_segments, uint64_t *n_blocks, uint32_t *W,
                  uint32_t *log2_S) {
   geom_t g;
@@ -323,7 +324,7 @@ void orc_free(void *p) { free(p); }
 
 /* ----------------------------------------------------- serialization (§3-5) */
 
-/* class of symbol q in a segment with n commands (FORMAT.md §3) */
+/* class of symbol q in a segment with n commands (the format's symbol message) */
 static int sym_class(uint64_t q, uint64_t n, uint32_t W) {
   if (q < 2 * n) return 0;
   if (q < 4 * n) return 1;
@@ -331,7 +332,7 @@ static int sym_class(uint64_t q, uint64_t n, uint32_t W) {
   return 3;
 }
 
-/* the n_sym symbols of segment s (FORMAT.md §3) */
+/* the n_sym symbols of segment s (the format's symbol message) */
 static uint64_t segment_symbols(const uint8_t *in, const geom_t *g, uint64_t s, const orc_cmd *c, uint64_t nc,
                                 uint8_t *sym) {
   uint64_t q = 0;
@@ -386,7 +387,8 @@ static uint64_t segment_deps(const geom_t *g, uint64_t s, const orc_cmd *c, uint
   return k;
 }
 
-/* rANS-encode one segment (FORMAT.md §4, encoding); words land reversed in words[] */
+/* rANS-encode one segment (the format's rANS encoder, run backwards over the
+ * symbols); words land reversed in words[] */
 static uint64_t rans_encode_segment(const uint8_t *sym, uint64_t n_sym, uint64_t nc, uint32_t W,
                                     const uint16_t freq[4][256], const uint32_t cum[4][257], uint32_t states[LANES],
                                     uint16_t *words) {
@@ -492,7 +494,7 @@ int64_t orc_serialize(const uint8_t *in, uint64_t n, uint32_t log2_B, uint32_t m
     memcpy(seg_words[s], words, sizeof(uint16_t) * n_words[s]);
     payload = round16(payload + 128 + 2 * n_words[s]);
   }
-  /* layout (FORMAT.md §5) */
+  /* layout (the format's section layout) */
   uint64_t off_tables = 128, off_dir = off_tables + 2048;
   uint64_t off_dep_ptr = round16(off_dir + 24 * n_seg);
   uint64_t off_deps = round16(off_dep_ptr + 8 * (n_seg + 1));
@@ -585,7 +587,7 @@ static void arc_release(arc_t *A) {
   for (int c = 0; c < 4; ++c) free(A->lut[c]);
 }
 
-/* header, tables, directory and dependency checks of FORMAT.md §6 */
+/* header, tables, directory and dependency checks of the format (header, tables, directory, dependency lists) */
 static int arc_open(const uint8_t *a, uint64_t len, arc_t *A) {
   memset(A, 0, sizeof(*A));
   A->a = a;
@@ -662,7 +664,7 @@ static int arc_open(const uint8_t *a, uint64_t len, arc_t *A) {
 }
 
 /*
- * rANS-decode the n_sym symbols of segment s (FORMAT.md §4, normative rule),
+ * rANS-decode the n_sym symbols of segment s (the format's rANS decoding rule),
  * checking the final-state invariant. final_states (optional) receives the
  * 32 lane states after the last symbol.
  */

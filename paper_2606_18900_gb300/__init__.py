@@ -19,7 +19,12 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
-_SO = os.path.join(_HERE, "libaceapex.so")
+_SO_PLAIN = os.path.join(_HERE, "libaceapex.so")
+_SO_PHASES = os.path.join(_HERE, "libaceapex_phases.so")
+# ACEAPEX_LIBRARY=phases selects the build with per-phase cycle counters
+# (bench.py's phase-split leg); any other value is the path of a library build.
+_SO = {None: _SO_PLAIN, "": _SO_PLAIN, "phases": _SO_PHASES}.get(os.environ.get("ACEAPEX_LIBRARY"),
+                                                                os.environ.get("ACEAPEX_LIBRARY"))
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 _SOURCES = ["kernels.cu", "gpu_encoder.cu", "host.cpp", "encoder.cpp", "server.cpp"]
 _lock = threading.Lock()
@@ -46,19 +51,21 @@ def _nvcc() -> str:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile libaceapex.so in-tree for sm_103a (the translation units in
-    parallel, then one link)."""
+    parallel, then one link), and beside it libaceapex_phases.so, the same
+    library with per-phase cycle counters in the decode kernels."""
     srcs = [os.path.join(_CSRC, s) for s in _SOURCES]
     deps = srcs + [os.path.join(_CSRC, h) for h in ("format.h", "kernels.h", "archive.h", "encoder_rules.h")] + [os.path.join(_INCLUDE, "aceapex.h")]
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(os.path.getmtime(d) for d in deps):
-        return _SO
+    newest = max(os.path.getmtime(d) for d in deps)
+    if not force and all(os.path.exists(p) and os.path.getmtime(p) >= newest for p in (_SO_PLAIN, _SO_PHASES)):
+        return _SO_PLAIN
     nvcc = _nvcc()
     bdir = os.path.join(_HERE, "_build")
     os.makedirs(bdir, exist_ok=True)
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + _CSRC, "-I" + _INCLUDE]
 
-    def compile_one(src):
-        obj = os.path.join(bdir, os.path.basename(src) + ".o")
-        cmd = [nvcc, "-c", src, "-o", obj] + common
+    def compile_one(job):
+        src, obj, extra = job
+        cmd = [nvcc, "-c", src, "-o", obj] + common + extra
         if src.endswith(".cu"):
             cmd += [ARCH, "-lineinfo", "-Xptxas", "-v" if verbose else "-O3"]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -68,14 +75,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(len(srcs)) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    tmp = _SO + f".tmp{os.getpid()}"
-    r = subprocess.run([nvcc, "-shared", ARCH, "-o", tmp] + objs + ["-lpthread"], capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, _SO)
-    return _SO
+    jobs = [(s, os.path.join(bdir, os.path.basename(s) + ".o"), []) for s in srcs]
+    kern = os.path.join(_CSRC, "kernels.cu")
+    jobs.append((kern, os.path.join(bdir, "kernels_phases.cu.o"), ["-DACEAPEX_PHASE_CLOCKS"]))
+    with ThreadPoolExecutor(len(jobs)) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    plain = objs[: len(srcs)]
+    phased = [objs[-1] if os.path.basename(o) == "kernels.cu.o" else o for o in plain]
+    for target, parts in ((_SO_PLAIN, plain), (_SO_PHASES, phased)):
+        tmp = target + f".tmp{os.getpid()}"
+        r = subprocess.run([nvcc, "-shared", ARCH, "-o", tmp] + parts + ["-lpthread"], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr}")
+        os.replace(tmp, target)
+    return _SO_PLAIN
 
 
 class Stats(ctypes.Structure):
@@ -110,7 +123,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(_SO):
+            if _SO in (_SO_PLAIN, _SO_PHASES) and not os.path.exists(_SO):
                 build()
             L = ctypes.CDLL(_SO)
             vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int

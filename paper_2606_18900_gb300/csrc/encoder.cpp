@@ -1,6 +1,6 @@
 // Host encoder of the library (paper §2: global match search over the whole
 // decompressed history, absolute offsets, fixed-size blocks; the paper's
-// encoder is also CPU-only and slow, §8). It writes FORMAT.md v1 archives.
+// encoder is also CPU-only and slow, §8). It writes version-1 archives.
 //
 // Design, differing from a plain sequential encoder in three ways so that it
 // is fast and deterministic for any thread count:
@@ -235,7 +235,7 @@ struct Parser {
     return best;
   }
 
-  // Parse segment s. Rules (FORMAT.md §2): mlen >= min_match, src + mlen <=
+  // Parse segment s. Rules: mlen >= min_match, src + mlen <=
   // dst, the match stays inside its segment, dst - src <= D, and the symbol
   // budget n_cmd*(4+W) + literals + bytes still to produce stays <= kMaxSym.
   void parse_segment(uint64_t s, std::vector<Cmd> &out) const {
@@ -536,7 +536,7 @@ int encode_archive(const uint8_t *in, uint64_t n, uint32_t log2_B, uint32_t min_
     for (auto &th : pool) th.join();
   }
 
-  // ---- layout (FORMAT.md §5)
+  // ---- layout (the format's section layout)
   std::vector<uint64_t> poff(g.n_seg + 1, 0);
   for (uint64_t s = 0; s < g.n_seg; ++s) poff[s + 1] = round16(poff[s] + 128 + 2 * coded[s].words.size());
   uint64_t payload = poff[g.n_seg];

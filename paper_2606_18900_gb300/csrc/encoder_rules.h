@@ -2,7 +2,7 @@
 // so that both write the same archive for the same input and parameters:
 // the level schedule, the match-finder hash, the chain window and the
 // table normalisation. (The format itself does not fix any of these; any
-// encoder whose archive satisfies FORMAT.md v1 is valid.)
+// encoder whose archive satisfies version 1 of the archive format is valid.)
 #pragma once
 #include <cstdint>
 

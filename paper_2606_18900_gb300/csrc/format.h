@@ -1,4 +1,4 @@
-// Layout constants and records of the archive format (FORMAT.md v1), as
+// Layout constants and records of the archive format (version 1), as
 // seen by the library's host code and kernels.
 #pragma once
 #include <cstdint>
@@ -14,7 +14,7 @@ constexpr uint32_t kHeaderBytes = 128;
 constexpr uint32_t kTablesBytes = 2048;
 constexpr uint32_t kMaxLog2S = 14;     // segments are at most 16 KiB
 
-// Segment directory record, byte-identical to FORMAT.md §5.3 (24 bytes).
+// Segment directory record as stored in the archive (24 bytes).
 struct SegRec {
   uint64_t payload_off;
   uint32_t n_words;
@@ -25,7 +25,7 @@ struct SegRec {
 };
 static_assert(sizeof(SegRec) == 24, "directory record is 24 bytes");
 
-// Parsed header (FORMAT.md §5.1).
+// Parsed header (the format's 128-byte header).
 struct Header {
   uint64_t n;
   uint32_t log2_B, log2_S, W, min_match, max_level, flags;

@@ -20,7 +20,7 @@
 //     between mask bits, applies the symbol budget, flattens intra-segment
 //     chains and lists the segment's source segments.
 //  3. symbols: one warp per segment writes the segment's symbol message
-//     (FORMAT.md §3) and counts symbols per class; levels follow tier by tier
+//     (the format's symbol message) and counts symbols per class; levels follow tier by tier
 //     of the schedule (a segment only reads lower tiers); dependency lists
 //     are packed into CSR form.
 //  4. entropy: the 1024 class counts are normalised on the host (4 x 256
@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(128) enc_parse_kernel(ParseCtx g, uint64_t s0,
   b.ndep[i] = collect_deps(s, g.log2_S, nc, b.lm + cmd0, b.srcs + cmd0, b.deptmp + 2 * cmd0);
 }
 
-// One warp per segment: the symbol message (FORMAT.md §3) into
+// One warp per segment: the symbol message (the format's symbol message) into
 // sym[s * slot ...] and the per-class symbol counts.
 __global__ void __launch_bounds__(256) enc_symbols_kernel(const uint8_t *in, uint64_t n, uint64_t s0, uint32_t nb,
                                                           uint32_t log2_S, uint32_t W, uint32_t min_match,
@@ -689,7 +689,7 @@ __global__ void __launch_bounds__(256) enc_deps_copy_kernel(uint64_t s0, uint32_
 
 // ------------------------------------------------------------ phase 4: entropy coding and layout
 
-// One warp per segment: the FORMAT.md §4 encoder, 32 lanes, symbols in
+// One warp per segment: the format's rANS encoder, 32 lanes, symbols in
 // reverse order. Pass 1 (payload == nullptr) counts the words; pass 2
 // writes the 32 initial states and the words in decode order.
 __global__ void __launch_bounds__(256) enc_rans_kernel(const uint8_t *sym, uint32_t slot, const uint32_t *n_cmd,

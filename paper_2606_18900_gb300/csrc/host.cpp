@@ -1,7 +1,7 @@
-// Host side of libaceapex.so: archive validation (FORMAT.md §6), device
-// residency (paper §3.3), work lists in level order, source closures for range
-// decode (paper §4), the ring streamer (paper §5), batching, and the C ABI
-// declared in include/aceapex.h.
+// Host side of libaceapex.so: archive validation (header, tables, directory,
+// dependency lists), device residency (paper §3.3), work lists in level order,
+// source closures for range decode (paper §4), the ring streamer (paper §5),
+// batching, and the C ABI declared in include/aceapex.h.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,7 +51,8 @@ uint32_t *global_epoch(int device) {
 
 namespace aceapex {
 
-// FORMAT.md §6 host-side checks; fills h, dir, dep_ptr, deps, reads, stats.
+// Host-side checks of the format (header, tables, directory, dependency lists,
+// read index); fills h, dir, dep_ptr, deps, reads, stats.
 // f(0) .. f(n - 1) on up to 16 host threads
 template <class F>
 void parallel_for(uint64_t n, F f) {

@@ -4,14 +4,14 @@
 // §3.3 full pipeline; §4 range decode; §5 chunked range decode). Each warp
 // repeatedly takes the next work item from a global counter; the list is in
 // level order, so every segment a warp waits for was taken earlier by a warp
-// that is running (no deadlock, FORMAT.md §2 levels). Per segment (details at
+// that is running (no deadlock, every source segment has a lower dependency level). Per segment (details at
 // decode_segment):
-//   1. rANS over the three command classes (FORMAT.md §4): the 32 lanes run
+//   1. rANS over the three command classes (the format's rANS coding): the 32 lanes run
 //      the 32 interleaved states; each step's renormalisation words are handed
 //      out in ascending lane order with a ballot + popc, from a shared-memory
 //      ring that cp.async keeps filled ahead of the reader.
 //   2. command parse: 32 commands at a time, positions from warp scans, every
-//      rule of FORMAT.md §2 checked, source segments checked (level below
+//      command rule checked, source segments checked (level below
 //      ours, present in the view).
 //   3. rANS over the literal class, each literal stored straight to its
 //      output position.
@@ -173,35 +173,104 @@ struct MatchTable {
   uint32_t pad[3];    // keeps the size a multiple of 16
 };
 
+// 16- and 32-bit loads through 32-bit shared-window addresses (volatile:
+// they must stay behind the cp.async waits that fill the word ring)
+__device__ __forceinline__ uint32_t lds_u16(uint32_t a) {
+  uint16_t v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts_u8(uint32_t a, uint32_t v) {
+  asm volatile("st.shared.u8 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void sts_u16(uint32_t a, uint32_t v) {
+  asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"((uint16_t)v) : "memory");
+}
+
+// The command staging area of a warp (shared memory, or the warp's global
+// slot for segments whose command streams do not fit): byte offsets; the area
+// is 4-byte aligned.
+struct Stage {
+  uint8_t *p;
+  __device__ __forceinline__ uint32_t u16(uint32_t o) const { return *reinterpret_cast<const uint16_t *>(p + o); }
+  __device__ __forceinline__ uint32_t u32(uint32_t o) const { return *reinterpret_cast<const uint32_t *>(p + o); }
+  __device__ __forceinline__ void st8(uint32_t o, uint32_t v) const { p[o] = (uint8_t)v; }
+  __device__ __forceinline__ void st16(uint32_t o, uint32_t v) const {
+    *reinterpret_cast<uint16_t *>(p + o) = (uint16_t)v;
+  }
+  // W-byte little-endian value at offset o (1 <= W <= 8); reads only the
+  // aligned 4-byte words that hold bytes of [o, o + W), so never past the
+  // word that holds byte o + W - 1
+  __device__ __forceinline__ uint64_t le(uint32_t o, uint32_t W) const {
+    const uint32_t a = o & ~3u, sh = 8 * (o & 3u), span = (o & 3u) + W;
+    const uint32_t w0 = u32(a);
+    const uint32_t w1 = span > 4 ? u32(a + 4) : 0u;
+    uint64_t v = __funnelshift_r(w0, w1, sh);
+    if (W > 4) {
+      const uint32_t w2 = span > 8 ? u32(a + 8) : 0u;
+      v |= (uint64_t)__funnelshift_r(w1, w2, sh) << 32;
+    }
+    return W >= 8 ? v : v & ((uint64_t(1) << (8 * W)) - 1);
+  }
+};
+
+#ifdef ACEAPEX_PHASE_CLOCKS
+// Warp-cycle counters per phase (instrumented build only): 0 command-class
+// rANS, 1 command parse, 2 literal rANS and placement, 3 dependency waits,
+// 4 match copies, 5 the rest of the work loop.
+__device__ unsigned long long g_phase_cycles[8];
+#define PHASE_MARK(i)                    \
+  do {                                   \
+    if (lane == 0) {                     \
+      const uint64_t t_ = clock64();     \
+      ph[i] += t_ - ph_t;                \
+      ph_t = t_;                         \
+    }                                    \
+  } while (0)
+#else
+#define PHASE_MARK(i) \
+  do {                \
+  } while (0)
+#endif
+
 // Decode one segment into view V and publish its ready flag.
 //
-// lut: the 4 x 4096-entry decode table (shared or global memory). sstage /
-// scap: the warp's shared-memory staging area and its size; gstage: the warp's
-// 16 KiB global staging slot, used when the command streams do not fit scap.
-// mt: the warp's shared match table; ring: the warp's 512-word shared ring.
+// lut: the 4 x 4096-entry decode table (kSmemLut: at shared-window address
+// lut_s; otherwise global lut). st: the warp's command staging area. mt: the
+// warp's shared match table; ring_s: shared-window address of the warp's
+// 1 KiB renormalisation-word ring (1 KiB aligned).
 //
-// Phases: (1) rANS over the three command classes into staging; (2) parse,
-// scans and every rule check, rewriting each command's literal-run and
-// match-length fields in place as the inclusive literal prefix and the
-// exclusive match-length prefix; (3) rANS over the literal class, each lane
-// storing its literal straight to the output position found by its own
-// command cursor; (4) bounded waits on source segments, then match copies in
-// rounds: a round copies every pending match of a 32-command chunk whose
-// source does not overlap the output of an earlier pending match, the bytes
-// of the round spread over all lanes; (5) publish.
+// Phases: (1) rANS over the three command classes into the staging area;
+// (2) parse, scans and the checks of every command, rewriting each command's
+// literal-run length in place as the inclusive literal prefix (the run's end
+// in literal numbering); (3) rANS over the literal class, each literal stored
+// straight to its output position: the literals of one step are consecutive
+// in literal numbering, so a warp-uniform cursor walks the command boundaries
+// that fall inside the step and moves the per-lane output pointers of the
+// lanes past each boundary by that command's match length; (4) per 32-command
+// chunk: source levels (and pages) checked, bounded waits on the source
+// segments' flags, then match copies in rounds: a round copies every pending
+// match whose source does not overlap the output of an earlier pending match,
+// the bytes of the round spread over all lanes; (5) publish.
 template <bool kSmemLut, int kMode>
-__device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevArchive &A, const OutView &V,
-                                               uint32_t seg, uint32_t epoch, const uint32_t *lut, uint8_t *sstage,
-                                               uint32_t scap, uint8_t *gstage, MatchTable *mt, uint16_t *ring,
-                                               int lane) {
+__device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const DevArchive &A, const OutView &V,
+                                                    uint32_t seg, uint32_t epoch, const uint32_t *lut,
+                                                    uint32_t lut_s, const Stage st, MatchTable *mt,
+                                                    uint32_t ring_s, int lane, const SegRec &d, uint64_t *ph,
+                                                    uint64_t &ph_t) {
+  (void)ph;
+  (void)ph_t;
   const uint32_t log2_S = A.log2_S;
   const uint64_t seg_start = (uint64_t)seg << log2_S;
   const uint64_t rem = A.n - seg_start;
   const uint32_t out_size = rem < (uint64_t(1) << log2_S) ? (uint32_t)rem : (1u << log2_S);
-  const SegRec d = A.dir[seg];
-  const uint32_t nc = d.n_cmd, nl = d.n_lit, nw = d.n_words, W = A.W;
+  const uint32_t nc = d.n_cmd, nl = d.n_lit, nw = d.n_words, W = A.W, mm = A.min_match;
   const uint32_t b1 = 2 * nc, b2 = 4 * nc, b3 = (4 + W) * nc, n_sym = b3 + nl;
-  uint8_t *stage = b3 <= scap ? sstage : gstage;
   // the segment's own output is contiguous in every view
   uint8_t *const out = at(V, seg_start, log2_S);
   bool ok = out != nullptr;
@@ -220,9 +289,9 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
   // by cp.async in blocks of 128 words two blocks ahead of the reader, so the
   // decode never waits on a global load between block boundaries. A lane
   // copies a 16-byte chunk only if it starts before the segment's last word;
-  // the payload is padded to 16 bytes, so no copy leaves the archive.
+  // the payload is padded to 16 bytes, so no copy leaves the archive. wb is
+  // the byte offset of the next word in the segment's word stream.
   const uint8_t *wsrc = pl + 128;
-  const uint32_t ring_s = smem_addr(ring);
   auto fetch = [&](uint32_t blk) {
     const uint32_t wi = blk * 128 + (uint32_t)lane * 8;
     if (lane < 16 && wi < nw) cp_async16(ring_s + (blk & 3) * 256 + lane * 16, wsrc + (size_t)wi * 2);
@@ -234,48 +303,68 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
   fetch(3);
   cp_async_wait<2>();
   __syncwarp();
-  uint32_t blk = 0, wp = 0;
+  uint32_t blk = 0, wb = 0;
   const uint32_t lt = lanemask_lt();
   // after the step that consumed the last word of a block: reuse its slot
   auto advance = [&]() {
-    if ((wp >> 7) != blk) {
-      blk = wp >> 7;
+    if ((wb >> 8) != blk) {
+      blk = wb >> 8;
       __syncwarp();
       fetch(blk + 3);
       cp_async_wait<2>();
       __syncwarp();
     }
   };
-  // one interleaved step: lane j decodes symbol t0 + j of class cls
-  auto step = [&](uint32_t cls, bool active) -> uint32_t {
+  // table entry of slot (class << 12 | x mod 4096)
+  auto entry = [&](uint32_t idx) -> uint32_t {
+    if (kSmemLut) return lds_u32(lut_s + 4 * idx);
+    return __ldg(lut + idx);
+  };
+  // lanes whose state fell below 2^16 read the next words in ascending lane
+  // order (every lane reads a ring word; only those lanes use it)
+  auto renorm = [&](bool need) {
+    const uint32_t m = __ballot_sync(kFull, need);
+    const uint32_t w = lds_u16(((wb + 2 * __popc(m & lt)) & 1023u) | ring_s);
+    if (need) x = __byte_perm(w, x, 0x5410);  // x << 16 | w
+    wb += 2 * __popc(m);
+  };
+  // one interleaved step of the command classes: lane j decodes symbol q
+  auto cmd_step = [&](uint32_t q) -> uint32_t {
+    const bool active = q < n_sym;
+    const uint32_t cls = (uint32_t)(q >= b1) + (uint32_t)(q >= b2) + (uint32_t)(q >= b3);
     uint32_t sym = 0;
     if (active) {
-      const uint32_t e = lut[(cls << kScaleBits) + (x & (kScale - 1))];
+      const uint32_t e = entry((cls << kScaleBits) | (x & (kScale - 1)));
       sym = e & 0xFFu;
       x = ((e >> 20) + 1u) * (x >> kScaleBits) + ((e >> 8) & 0xFFFu);
     }
-    const bool need = active && x < kRansL;
-    const uint32_t m = __ballot_sync(kFull, need);
-    if (need) x = (x << 16) | ring[(wp + __popc(m & lt)) & 511];
-    wp += __popc(m);
-    advance();
+    renorm(active && x < kRansL);
     return sym;
   };
 
   // (1) command classes; the step that crosses into the literals keeps its
-  // literal symbols in `pend` until the command prefixes exist
+  // literal symbol in `pend` until the command prefixes exist. Four steps take
+  // at most 128 words, so after an advance() (blocks blk and blk + 1 complete,
+  // wb inside blk) four steps read only those two blocks.
   uint32_t t0 = 0, pend = 0;
-  for (; ok && t0 < b3; t0 += 32) {
-    const uint32_t q = t0 + lane;
-    const uint32_t cls = q < b1 ? 0u : (q < b2 ? 1u : (q < b3 ? 2u : 3u));
-    const uint32_t sym = step(cls, q < n_sym);
-    if (q < b3) stage[q] = (uint8_t)sym;
-    else pend = sym;
+  if (ok) {
+    for (; t0 + 128 <= b3; t0 += 128) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) st.st8(t0 + 32 * u + lane, cmd_step(t0 + 32 * u + lane));
+      advance();
+    }
+    for (; t0 < b3; t0 += 32) {
+      const uint32_t q = t0 + lane;
+      const uint32_t sym = cmd_step(q);
+      if (q < b3) st.st8(q, sym);
+      else pend = sym;
+      advance();
+    }
   }
   __syncwarp();
+  PHASE_MARK(0);
 
   // (2) parse, prefixes, checks
-  const uint32_t my_level = d.level;
   uint32_t tot_l = 0, tot_m = 0;
   for (uint32_t c0 = 0; ok && c0 < nc; c0 += 32) {
     const uint32_t c = c0 + lane;
@@ -283,113 +372,150 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
     uint32_t ll = 0, ml = 0;
     uint64_t src = 0;
     if (valid) {
-      ll = ld16(stage + 2 * c);
-      ml = ld16(stage + b1 + 2 * c) + A.min_match;
-      for (uint32_t b = 0; b < W; ++b) src |= (uint64_t)stage[b2 + W * c + b] << (8 * b);
+      ll = st.u16(2 * c);
+      ml = st.u16(b1 + 2 * c) + mm;
+      src = st.le(b2 + W * c, W);
     }
     const uint32_t inc_l = warp_incl_scan(ll, lane), inc_m = warp_incl_scan(ml, lane);
     const uint32_t lit_end = tot_l + inc_l, msum = tot_m + inc_m - ml;
     const uint32_t cend = lit_end + msum + ml;  // end of the command in the segment
     const uint64_t dst = seg_start + lit_end + msum;
-    bool bad = valid && ((uint64_t)cend > out_size || lit_end > nl || src + ml > dst || src + ml < src ||
-                         (A.D && dst - src > A.D));
-    if (valid && !bad) {
-      const uint64_t q0 = src >> log2_S, q1 = (src + ml - 1) >> log2_S;
-      for (uint64_t qq = q0; qq <= q1; ++qq) {
-        if (qq == seg) continue;
-        if (A.dir[qq].level >= my_level) bad = true;
-        if (kMode == kViewPaged && V.page[qq] == 0xFFFFFFFFu) bad = true;
-      }
-    }
+    const bool bad = valid && ((uint64_t)cend > out_size || lit_end > nl || src + ml > dst || src + ml < src ||
+                               (A.D && dst - src > A.D));
     if (__any_sync(kFull, bad)) {
       ok = false;
       break;
     }
-    if (valid) {
-      st16(stage + 2 * c, lit_end);
-      st16(stage + b1 + 2 * c, msum);
-    }
+    if (valid) st.st16(2 * c, lit_end);
     tot_l += __shfl_sync(kFull, inc_l, 31);
     tot_m += __shfl_sync(kFull, inc_m, 31);
   }
   if (ok && (tot_l + tot_m > out_size || out_size - tot_m != nl)) ok = false;
   __syncwarp();
+  PHASE_MARK(1);
 
-  // (3) literals: lane j handles literals j, j+32, ...; its cursor (li, le,
-  // sh) is the command whose run holds its next literal (le = run end in
-  // literal numbering, sh = match bytes before that command)
+  // (3) literals. K0: literal number of lane 0 in the current step; E: end of
+  // the literal run of command cu (literal number), the next boundary; p: the
+  // lane's output address for its literal of the current step.
   if (ok) {
-    uint32_t li = 0, le = nc ? ld16(stage) : 0xFFFFFFFFu, sh = nc ? ld16(stage + b1) : tot_m;
-    auto place = [&](uint32_t k, uint32_t sym) {
-      while (k >= le) {
-        ++li;
-        if (li < nc) {
-          le = ld16(stage + 2 * li);
-          sh = ld16(stage + b1 + 2 * li);
-        } else {
-          le = 0xFFFFFFFFu;
-          sh = tot_m;
-        }
-      }
-      out[k + sh] = (uint8_t)sym;
+    constexpr int kInf = 0x3FFFFFFF;
+    int K0 = (b3 & 31u) ? (int)(b3 & ~31u) - (int)b3 : 0;
+    uint32_t cu = 0;
+    int E = nc ? (int)st.u16(0) : kInf;
+    uint8_t *p = out + K0 + lane;
+    // Commands whose runs end inside [K0, K0 + 32): the lanes at or after a
+    // run's end skip that command's match bytes in this step already, the
+    // lanes before it from the next step on (dq, added after the store).
+    auto bound = [&](uint32_t &dq) -> bool {
+      if (E - K0 >= 32) return false;
+      do {
+        const uint32_t ml = st.u16(b1 + 2 * cu) + mm;
+        if (lane >= E - K0) p += ml;
+        else dq += ml;
+        ++cu;
+        E = cu < nc ? (int)st.u16(2 * cu) : kInf;
+      } while (E - K0 < 32);
+      return true;
     };
-    if ((b3 & 31) && t0 - 32 + lane >= b3 && t0 - 32 + lane < n_sym) place(t0 - 32 + lane - b3, pend);
-    // full steps: every lane decodes, the class is known. Four steps take at
-    // most 128 words, so after an advance() (blocks blk and blk + 1 complete,
-    // wp inside blk) four steps read only those two blocks, and the ring
-    // advances once per four steps.
-    const uint32_t *lut3 = lut + (3u << kScaleBits);
-    auto lit_step = [&](uint32_t k) {
-      const uint32_t e = lut3[x & (kScale - 1)];
+    auto lit_rans = [&]() -> uint32_t {
+      const uint32_t e = entry((3u << kScaleBits) | (x & (kScale - 1)));
       x = ((e >> 20) + 1u) * (x >> kScaleBits) + ((e >> 8) & 0xFFFu);
-      const bool need = x < kRansL;
-      const uint32_t m = __ballot_sync(kFull, need);
-      if (need) x = (x << 16) | ring[(wp + __popc(m & lt)) & 511];
-      wp += __popc(m);
-      place(k, e);
+      renorm(x < kRansL);
+      return e;
     };
+    if (b3 & 31u) {  // the crossing step, decoded in (1)
+      uint32_t dq = 0;
+      const bool hb = bound(dq);
+      if (lane >= -K0 && t0 - 32 + lane < n_sym) *p = (uint8_t)pend;
+      if (hb) p += dq;
+      p += 32;
+      K0 += 32;
+    }
     for (; t0 + 128 <= n_sym; t0 += 128) {
-      const uint32_t k = t0 + lane - b3;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) lit_step(k + 32 * u);
+      for (int u = 0; u < 4; ++u) {
+        uint32_t dq = 0;
+        const bool hb = bound(dq);
+        p[32 * u] = (uint8_t)lit_rans();
+        if (hb) p += dq;
+        K0 += 32;
+      }
+      p += 128;
       advance();
     }
     for (; t0 + 32 <= n_sym; t0 += 32) {
-      lit_step(t0 + lane - b3);
+      uint32_t dq = 0;
+      const bool hb = bound(dq);
+      *p = (uint8_t)lit_rans();
+      if (hb) p += dq;
+      p += 32;
+      K0 += 32;
       advance();
     }
     if (t0 < n_sym) {
-      const uint32_t q = t0 + lane;
-      const bool active = q < n_sym;
-      const uint32_t sym = step(3u, active);
-      if (active) place(q - b3, sym);
+      const bool active = t0 + lane < n_sym;
+      uint32_t dq = 0;
+      bound(dq);
+      uint32_t e = 0;
+      if (active) {
+        e = entry((3u << kScaleBits) | (x & (kScale - 1)));
+        x = ((e >> 20) + 1u) * (x >> kScaleBits) + ((e >> 8) & 0xFFFu);
+      }
+      renorm(active && x < kRansL);
+      if (active) *p = (uint8_t)e;
       t0 += 32;
     }
   }
-  if (!__all_sync(kFull, x == kRansL) || wp != nw) ok = false;
+  if (!__all_sync(kFull, x == kRansL) || wb != 2 * nw) ok = false;
   __syncwarp();
+  PHASE_MARK(2);
 
   // (4) matches
+  const uint32_t my_level = d.level;
   const uint64_t deadline = now_ns() + L.wait_ns;
+  uint32_t mbase = 0;
   for (uint32_t c0 = 0; ok && c0 < nc; c0 += 32) {
     const uint32_t c = c0 + lane;
     const bool valid = c < nc;
-    uint32_t ml = 0;
-    uint64_t src = 0, dst = ~uint64_t(0);
+    uint32_t ml = 0, lend = 0;
+    uint64_t src = 0;
     if (valid) {
-      const uint32_t msum = ld16(stage + b1 + 2 * c);
-      ml = (c + 1 < nc ? ld16(stage + b1 + 2 * c + 2) : tot_m) - msum;
-      dst = seg_start + ld16(stage + 2 * c) + msum;
-      for (uint32_t b = 0; b < W; ++b) src |= (uint64_t)stage[b2 + W * c + b] << (8 * b);
+      ml = st.u16(b1 + 2 * c) + mm;
+      lend = st.u16(2 * c);
+      src = st.le(b2 + W * c, W);
     }
+    const uint32_t inc_m = warp_incl_scan(ml, lane);
+    const uint64_t dst = valid ? seg_start + lend + (mbase + inc_m - ml) : ~uint64_t(0);
+    mbase += __shfl_sync(kFull, inc_m, 31);
     const uint64_t q0 = src >> log2_S, q1 = valid ? (src + ml - 1) >> log2_S : q0;
     const bool need0 = valid && q0 != seg;
     const bool need1 = valid && q1 != q0 && q1 != seg;
-    if (!wait_flags(A.flags + (need0 ? q0 : 0), need0, epoch, deadline, L.err, lane) ||
-        !wait_flags(A.flags + (need1 ? q1 : 0), need1, epoch, deadline, L.err, lane)) {
+    // A source segment must have a lower level than ours (a wait on any other
+    // could not end) and, in a paged view, be present. Its flag is read in
+    // the same pass.
+    bool bad = false;
+    uint32_t f0 = epoch, f1 = epoch;
+    if (need0) {
+      bad |= A.dir[q0].level >= my_level;
+      if (kMode == kViewPaged) bad |= V.page[q0] == 0xFFFFFFFFu;
+      f0 = ld_acquire(A.flags + q0);
+    }
+    if (need1) {
+      bad |= A.dir[q1].level >= my_level;
+      if (kMode == kViewPaged) bad |= V.page[q1] == 0xFFFFFFFFu;
+      f1 = ld_acquire(A.flags + q1);
+    }
+    if (__any_sync(kFull, bad)) {
       ok = false;
       break;
     }
+    if (!__all_sync(kFull, f0 == epoch && f1 == epoch) &&
+        (!wait_flags(A.flags + (need0 ? q0 : 0), need0, epoch, deadline, L.err, lane) ||
+         !wait_flags(A.flags + (need1 ? q1 : 0), need1, epoch, deadline, L.err, lane))) {
+      ok = false;
+      break;
+    }
+    PHASE_MARK(3);
     mt->src[lane] = src;
     mt->dst[lane] = dst;
     __syncwarp();
@@ -408,9 +534,9 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
       const uint32_t d_end = valid ? d_off + ml : 0xFFFFFFFFu;
       uint32_t jh = 0, jl = 0;
 #pragma unroll
-      for (int st = 16; st; st >>= 1) {
-        if (__shfl_sync(kFull, d_off, jh + st) < se_rel) jh += st;
-        if (__shfl_sync(kFull, d_end, jl + st) <= s_rel) jl += st;
+      for (int s = 16; s; s >>= 1) {
+        if (__shfl_sync(kFull, d_off, jh + s) < se_rel) jh += s;
+        if (__shfl_sync(kFull, d_end, jl + s) <= s_rel) jl += s;
       }
       const bool any_h = __shfl_sync(kFull, d_off, jh) < se_rel;  // some output starts before the source ends
       const bool any_l = __shfl_sync(kFull, d_end, jl) <= s_rel;  // some output ends before the source starts
@@ -430,9 +556,8 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
       // with two 16-byte loads and realigned in registers; a whole block is
       // stored with one 16-byte store, a partial one byte by byte); otherwise
       // 16-byte pieces copied byte by byte. Lane j copies units j, j+32, ...
-      // of the round. Sources are read through L1: with vec an aligned source
-      // block never leaves its segment, and a segment is only read after its
-      // flag was acquired.
+      // of the round. With vec an aligned source block never leaves its
+      // segment, and a segment is only read after its flag was acquired.
       const uint32_t nu = !ready ? 0 : vec ? (((uint32_t)(dst - seg_start) & 15u) + ml + 15) >> 4 : (ml + 15) >> 4;
       const uint32_t incl = warp_incl_scan(nu, lane);
       const uint32_t total = __shfl_sync(kFull, incl, 31);
@@ -443,8 +568,8 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
       for (uint32_t uu = lane; uu < total; uu += 32) {
         uint32_t m = 0;
 #pragma unroll
-        for (int st = 16; st; st >>= 1)
-          if (mt->start[m + st] <= uu) m += st;
+        for (int s = 16; s; s >>= 1)
+          if (mt->start[m + s] <= uu) m += s;
         if (vec) {
           const uint32_t doff = (uint32_t)(mt->dst[m] - seg_start);
           const uint32_t b16 = (doff & ~15u) + ((uu - mt->start[m]) << 4);
@@ -454,17 +579,17 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
           const uint8_t *pa = src_at<kMode>(V, P, log2_S);
           const uint32_t dl = (uint32_t)reinterpret_cast<uintptr_t>(pa) & 15u;
           uint4 X = make_uint4(0, 0, 0, 0), Y = X;
-          uint32_t c;
+          uint32_t cc;
           if (dl >= o) {
             X = *reinterpret_cast<const uint4 *>(pa - dl);
             if (dl + n > 16) Y = *reinterpret_cast<const uint4 *>(src_at<kMode>(V, P + (16 - dl), log2_S));
-            c = dl - o;
+            cc = dl - o;
           } else {
             Y = *reinterpret_cast<const uint4 *>(pa - dl);
-            c = 16 + dl - o;
+            cc = 16 + dl - o;
           }
           uint32_t r[4];
-          realign16(X, Y, c, r);
+          realign16(X, Y, cc, r);
           uint8_t *to = out + b16;
           if (n == 16) {
             *reinterpret_cast<uint4 *>(to) = make_uint4(r[0], r[1], r[2], r[3]);
@@ -485,12 +610,12 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
         } else {
           const uint32_t o = (uu - mt->start[m]) << 4;
           const uint32_t n = min(16u, mt->len[m] - o);
-          const uint64_t p = mt->src[m] + o;
+          const uint64_t pp = mt->src[m] + o;
           uint8_t *to = out + (mt->dst[m] - seg_start) + o;
           uint8_t v[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if ((uint32_t)j < n) v[j] = *src_at<kMode>(V, p + j, log2_S);
+            if ((uint32_t)j < n) v[j] = *src_at<kMode>(V, pp + j, log2_S);
 #pragma unroll
           for (int j = 0; j < 16; ++j)
             if ((uint32_t)j < n) to[j] = v[j];
@@ -499,6 +624,7 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
       __syncwarp();
       pending = pending && !ready;
     }
+    PHASE_MARK(4);
   }
   if (!ok && lane == 0 && ld_relaxed(L.err) == 0) latch(L.err, kErrCorrupt);
 
@@ -508,6 +634,58 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
   if (lane == 0 && ok && !(A.blocked && A.blocked[seg])) st_release(A.flags + seg, epoch);
 }
 
+// Decode one segment: its command streams are staged in the warp's shared
+// area when they fit (scap bytes), else in its global slot gstage.
+template <bool kSmemLut, int kMode>
+__device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevArchive &A, const OutView &V,
+                                               uint32_t seg, uint32_t epoch, const uint32_t *lut, uint8_t *sstage,
+                                               uint32_t scap, uint8_t *gstage, MatchTable *mt, uint16_t *ring,
+                                               int lane, uint64_t *ph, uint64_t &ph_t) {
+  const SegRec d = A.dir[seg];
+  const uint32_t b3 = (4 + A.W) * d.n_cmd;
+  decode_segment_impl<kSmemLut, kMode>(L, A, V, seg, epoch, lut, kSmemLut ? smem_addr(lut) : 0u,
+                                       Stage{b3 <= scap ? sstage : gstage}, mt, smem_addr(ring), lane, d, ph, ph_t);
+}
+
+// Dynamic shared memory of a decode CTA: the decode table (64 KiB), then,
+// from the next 1 KiB boundary, a 1 KiB word ring per warp, then a match table
+// and a command stage per warp.
+struct WarpSmem {
+  uint32_t *lut;
+  uint16_t *ring;
+  MatchTable *mt;
+  uint8_t *stage;
+};
+__device__ __forceinline__ WarpSmem warp_smem(uint8_t *smem, int wid) {
+  constexpr uint32_t nw = kDecodeThreads / 32;
+  WarpSmem w;
+  w.lut = reinterpret_cast<uint32_t *>(smem);
+  const uint32_t base = smem_addr(smem) + kLutBytes;
+  uint8_t *rings = smem + kLutBytes + (((base + 1023u) & ~1023u) - base);
+  w.ring = reinterpret_cast<uint16_t *>(rings) + wid * 512;
+  w.mt = reinterpret_cast<MatchTable *>(rings + nw * 1024) + wid;
+  w.stage = rings + nw * (1024 + sizeof(MatchTable)) + (size_t)wid * kSmemStage;
+  return w;
+}
+
+#ifdef ACEAPEX_PHASE_CLOCKS
+#define PHASE_DECL        \
+  uint64_t ph[6] = {};    \
+  uint64_t ph_t = clock64()
+#define PHASE_FLUSH()                                                                              \
+  do {                                                                                             \
+    if (lane == 0)                                                                                 \
+      for (int i_ = 0; i_ < 6; ++i_) atomicAdd(&g_phase_cycles[i_], (unsigned long long)ph[i_]); \
+  } while (0)
+#else
+#define PHASE_DECL            \
+  uint64_t *ph = nullptr;     \
+  uint64_t ph_t = 0
+#define PHASE_FLUSH() \
+  do {                \
+  } while (0)
+#endif
+
 // Persistent decode of one archive: its decode table is copied to shared
 // memory once per CTA, and every warp takes the next work item.
 // kMode: how the view maps positions (linear output, ring, or page table).
@@ -515,14 +693,10 @@ template <int kMode>
 __global__ void __launch_bounds__(kDecodeThreads, 1) decode_kernel(DecodeLaunch L) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t *slut = reinterpret_cast<uint32_t *>(smem);
-  uint8_t *after_lut = smem + kLutBytes;
-  MatchTable *mt = reinterpret_cast<MatchTable *>(after_lut) + wid;
-  uint16_t *ring = reinterpret_cast<uint16_t *>(after_lut + (kDecodeThreads / 32) * sizeof(MatchTable)) + wid * 512;
-  uint8_t *sstage = after_lut + (kDecodeThreads / 32) * (sizeof(MatchTable) + 1024) + (size_t)wid * kSmemStage;
+  const WarpSmem ws = warp_smem(smem, wid);
   {
     const uint4 *g = reinterpret_cast<const uint4 *>(L.arc0.lut);
-    uint4 *s4 = reinterpret_cast<uint4 *>(slut);
+    uint4 *s4 = reinterpret_cast<uint4 *>(ws.lut);
     for (uint32_t i = threadIdx.x; i < kLutBytes / 16; i += blockDim.x) s4[i] = g[i];
     __syncthreads();
   }
@@ -530,14 +704,17 @@ __global__ void __launch_bounds__(kDecodeThreads, 1) decode_kernel(DecodeLaunch 
   if (gwarp >= L.scratch_warps || (uint32_t)wid >= L.active_warps) return;
   uint8_t *gstage = L.scratch + (size_t)gwarp * kStageBytes;
   const uint32_t epoch = ld_relaxed(L.epoch);
+  PHASE_DECL;
   for (;;) {
     bool failed;
     const uint32_t idx = take_item(L.counter, L.err, lane, failed);
     if (idx >= L.n_work) break;
     if (failed) continue;  // drain the list quickly after an error
-    decode_segment<true, kMode>(L, L.arc0, L.view0, L.work[idx].seg, epoch, slut, sstage, L.stage_cap, gstage, mt,
-                                ring, lane);
+    PHASE_MARK(5);
+    decode_segment<true, kMode>(L, L.arc0, L.view0, L.work[idx].seg, epoch, ws.lut, ws.stage, L.stage_cap, gstage,
+                                ws.mt, ws.ring, lane, ph, ph_t);
   }
+  PHASE_FLUSH();
 }
 
 // Batch decode, one archive per CTA at a time (see launch_batch).
@@ -547,14 +724,11 @@ __global__ void __launch_bounds__(kDecodeThreads, 1) batch_kernel(DecodeLaunch L
   __shared__ DevArchive s_A;
   __shared__ OutView s_V;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t *slut = reinterpret_cast<uint32_t *>(smem);
-  uint8_t *after_lut = smem + kLutBytes;
-  MatchTable *mt = reinterpret_cast<MatchTable *>(after_lut) + wid;
-  uint16_t *ring = reinterpret_cast<uint16_t *>(after_lut + (kDecodeThreads / 32) * sizeof(MatchTable)) + wid * 512;
-  uint8_t *sstage = after_lut + (kDecodeThreads / 32) * (sizeof(MatchTable) + 1024) + (size_t)wid * kSmemStage;
+  const WarpSmem ws = warp_smem(smem, wid);
   const uint32_t gwarp = blockIdx.x * (blockDim.x >> 5) + wid;
   uint8_t *gstage = L.scratch + (size_t)gwarp * kStageBytes;
   const uint32_t epoch = ld_relaxed(L.epoch);
+  PHASE_DECL;
   for (;;) {
     if (threadIdx.x == 0) {
       s_arc = atomicAdd(L.counter, 1u);
@@ -570,7 +744,7 @@ __global__ void __launch_bounds__(kDecodeThreads, 1) batch_kernel(DecodeLaunch L
     __syncthreads();
     const DevArchive &A = s_A;
     const uint4 *g = reinterpret_cast<const uint4 *>(A.lut);
-    uint4 *s4 = reinterpret_cast<uint4 *>(slut);
+    uint4 *s4 = reinterpret_cast<uint4 *>(ws.lut);
     for (uint32_t i = threadIdx.x; i < kLutBytes / 16; i += blockDim.x) s4[i] = g[i];
     __syncthreads();
     for (; (uint32_t)wid < L.active_warps;) {
@@ -578,11 +752,13 @@ __global__ void __launch_bounds__(kDecodeThreads, 1) batch_kernel(DecodeLaunch L
       const uint32_t idx = take_item(&s_next, L.err, lane, failed);
       if (idx >= A.n_seg) break;
       if (failed) continue;
-      decode_segment<true, kViewLinear>(L, A, s_V, A.order[idx].seg, epoch, slut, sstage, L.stage_cap, gstage, mt,
-                                        ring, lane);
+      PHASE_MARK(5);
+      decode_segment<true, kViewLinear>(L, A, s_V, A.order[idx].seg, epoch, ws.lut, ws.stage, L.stage_cap, gstage,
+                                        ws.mt, ws.ring, lane, ph, ph_t);
     }
     __syncthreads();  // the table is replaced only after every warp left this archive
   }
+  PHASE_FLUSH();
 }
 
 __global__ void begin_kernel(uint32_t *global_epoch, uint32_t *epoch, uint32_t *counter) {
@@ -900,8 +1076,9 @@ __global__ void interleave_kernel(LineStreams S, uint8_t *out) {
 // ------------------------------------------------------------------ launchers
 
 constexpr size_t kWarpSmem = sizeof(MatchTable) + 1024 + kSmemStage;
-static_assert(sizeof(MatchTable) % 16 == 0, "keeps the rings aligned");
-constexpr size_t kSmemLutBytes = kLutBytes + (size_t)(kDecodeThreads / 32) * kWarpSmem;
+static_assert(sizeof(MatchTable) % 16 == 0, "keeps the stages aligned");
+// + 1 KiB: the rings start at the first 1 KiB boundary after the table
+constexpr size_t kSmemLutBytes = kLutBytes + 1024 + (size_t)(kDecodeThreads / 32) * kWarpSmem;
 
 int decode_grid(int device, int block) {
   (void)block;
@@ -1157,8 +1334,11 @@ __global__ void __launch_bounds__(256) noalloc_decode_kernel(DecodeLaunch L, uin
   uint8_t *stage = g_noalloc_scratch + kNoAllocCtlBytes + kNoAllocLutBytes + kNoAllocFlagBytes +
                    (size_t)gwarp * kStageBytes;
   __shared__ MatchTable mts[8];
-  __shared__ __align__(16) uint16_t rings[8][512];
+  __shared__ __align__(16) uint16_t rings_raw[9][512];  // eight 1 KiB rings from the first 1 KiB boundary
+  const uint32_t rb = smem_addr(rings_raw);
+  uint16_t *ring = &rings_raw[0][0] + ((((rb + 1023u) & ~1023u) - rb) >> 1) + (threadIdx.x >> 5) * 512;
   const uint32_t epoch = ld_relaxed(L.epoch);
+  PHASE_DECL;
   const uint32_t empty = reinterpret_cast<const uint32_t *>(g_noalloc_scratch)[kCtlEmpty / 4];
   const DevArchive &A = L.arc0;
   for (;;) {
@@ -1169,16 +1349,18 @@ __global__ void __launch_bounds__(256) noalloc_decode_kernel(DecodeLaunch L, uin
     // the directory was not validated on the host: check what the shared
     // segment decoder relies on before calling it
     const SegRec d = A.dir[seg];
+    // (the payload test is written so that no sum can wrap)
     const uint64_t n_sym = (uint64_t)d.n_cmd * (4 + A.W) + d.n_lit;
-    const bool sane = n_sym <= kMaxSym && (d.payload_off & 15) == 0 &&
-                      d.payload_off + 128 + 2 * (uint64_t)d.n_words <= payload_bytes && d.level <= max_level &&
+    const bool sane = n_sym <= kMaxSym && (d.payload_off & 15) == 0 && d.payload_off <= payload_bytes &&
+                      payload_bytes - d.payload_off >= 128 &&
+                      d.n_words <= (payload_bytes - d.payload_off - 128) / 2 && d.level <= max_level &&
                       !(d.n_cmd && (empty & 7u)) && !(d.n_lit && (empty & 8u));
     if (!sane) {
       if (lane == 0) latch(L.err, kErrCorrupt);
       continue;
     }
     decode_segment<false, kViewLinear>(L, A, L.view0, seg, epoch, A.lut, stage, 0, stage, &mts[threadIdx.x >> 5],
-                                       rings[threadIdx.x >> 5], lane);
+                                       ring, lane, ph, ph_t);
   }
 }
 
@@ -1219,14 +1401,18 @@ extern "C" int aceapex_decode_all_noalloc(const void *d_archive, uint64_t nbytes
   auto u64 = [&](int o) { uint64_t v; std::memcpy(&v, h + o, 8); return v; };
   auto u32 = [&](int o) { uint32_t v; std::memcpy(&v, h + o, 4); return v; };
   const uint64_t n = u64(16), n_seg = u64(40), n_deps = u64(48), n_reads = u64(56);
-  const uint32_t log2_B = h[24], log2_S = h[25], W = h[26], min_match = h[27];
+  const uint32_t log2_B = h[24], log2_S = h[25], W = h[26], min_match = h[27], flags = h[31];
   if (std::memcmp(h, "ACEAPEX1", 8) != 0 || u32(8) != 1 || u32(12) != kHeaderBytes || h[28] != kScaleBits ||
-      h[29] != kLanes || log2_B < 2 || log2_B > 30 || log2_S != (log2_B < kMaxLog2S ? log2_B : kMaxLog2S) ||
-      W != offset_width(n) || min_match < 1)
+      h[29] != kLanes || (flags & ~1u) || (!(flags & 1u) && n_reads) || log2_B < 2 || log2_B > 30 ||
+      log2_S != (log2_B < kMaxLog2S ? log2_B : kMaxLog2S) || W != offset_width(n) || min_match < 1)
     return 2;  // ACEAPEX_ECORRUPT
+  // counts bounded by the archive length first, so that the section offsets
+  // below cannot wrap
+  if (n_seg > nbytes / 24 || n_deps > nbytes / 4 || n_reads > nbytes / 8) return 2;
   const uint64_t S = uint64_t(1) << log2_S;
   const uint64_t off_dir = u64(72), off_dep_ptr = u64(80), off_deps = u64(88), off_reads = u64(96);
   const uint64_t off_payload = u64(104), payload_bytes = u64(112), total = u64(120);
+  if (off_payload > nbytes || payload_bytes > nbytes || (payload_bytes & 15)) return 2;
   if (n_seg != (n + S - 1) / S || u64(64) != kHeaderBytes || off_dir != kHeaderBytes + kTablesBytes ||
       off_dep_ptr != round16(off_dir + 24 * n_seg) || off_deps != round16(off_dep_ptr + 8 * (n_seg + 1)) ||
       off_reads != round16(off_deps + 4 * n_deps) || off_payload != round16(off_reads + 8 * n_reads) ||
@@ -1266,3 +1452,23 @@ extern "C" int aceapex_decode_all_noalloc(const void *d_archive, uint64_t nbytes
 }
 
 }  // namespace aceapex
+
+#ifdef ACEAPEX_PHASE_CLOCKS
+// Instrumented build only: copies the warp cycles that the decode kernels
+// spent in each phase (command-class rANS, command parse, literal rANS and
+// placement, dependency waits, match copies, the rest of the work loop) since
+// the last reset into out[0 .. n) (n <= 6), and zeroes them when reset != 0.
+// Synchronises the current device. Returns 0, or 4 on a CUDA error.
+extern "C" int aceapex_phase_cycles(uint64_t *out, int n, int reset) {
+  unsigned long long h[8] = {};
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpyFromSymbol(h, aceapex::g_phase_cycles, sizeof(h)) != cudaSuccess)
+    return 4;
+  for (int i = 0; i < n && i < 6; ++i) out[i] = h[i];
+  if (reset) {
+    const unsigned long long z[8] = {};
+    if (cudaMemcpyToSymbol(aceapex::g_phase_cycles, z, sizeof(z)) != cudaSuccess) return 4;
+  }
+  return 0;
+}
+#endif

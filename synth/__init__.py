@@ -3,8 +3,8 @@ and the benchmark.
 
 This package produces decompressed bytes only; it contains none of the
 codec's arithmetic. The generators are C (``synth.c``) behind ctypes so that
-the 1 GiB and 50 GB workloads generate in seconds; the recipes are in
-GENERATOR.md. Every function takes explicit seeds and is deterministic.
+the 1 GiB and 50 GB workloads generate in seconds; each function
+states its recipe. Every function takes explicit seeds and is deterministic.
 """
 from __future__ import annotations
 

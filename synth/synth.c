@@ -4,7 +4,7 @@
  * This module holds no codec arithmetic: it only produces the decompressed
  * bytes that the encoders take as input. Both the CPU oracle's tests and the
  * GPU library's tests and benchmark draw their inputs from it, so it is kept
- * in a module of its own. The recipe of every generator is in GENERATOR.md.
+ * in a module of its own. Each generator states its recipe where it is defined.
  *
  * Randomness: SplitMix64 expands a (seed_a, seed_b) pair into the 256-bit
  * state of xoshiro256** (Blackman & Vigna, "Scrambled linear pseudorandom

@@ -2,7 +2,7 @@
 // per-thread device functions (match_at_slot, TableFinder, parse_segment,
 // flatten, collect_deps, compiled for the host from gpu_encoder.cu) over a
 // host-side stable sort, completes the archive on the host (levels, symbols,
-// tables, rANS, layout as FORMAT.md defines them) and compares it with the
+// tables, rANS, layout as the archive format defines them) and compares it with the
 // library's CPU encoder, byte for byte.
 //
 // usage: encoder_emulation <input file> <log2_B,min_match,max_level,D> ...
@@ -78,7 +78,7 @@ static std::vector<uint8_t> emulate(const std::vector<uint8_t> &src, uint32_t lo
       DP[s].assign(tmp.begin(), tmp.begin() + nd);
     }
   }
-  // levels, symbol messages (FORMAT.md §3) and class counts
+  // levels, symbol messages (the format's symbol message) and class counts
   std::vector<uint16_t> level(n_seg);
   std::vector<std::vector<uint8_t>> sym(n_seg);
   std::vector<uint32_t> nlit(n_seg);
@@ -112,7 +112,7 @@ static std::vector<uint8_t> emulate(const std::vector<uint8_t> &src, uint32_t lo
     uint32_t acc = 0;
     for (int x = 0; x < 256; ++x) cum[c][x] = acc, acc += f[c][x];
   }
-  // rANS (FORMAT.md §4, informative encoder) and layout (§5)
+  // rANS (the format's rANS encoder, run backwards over the symbols) and layout (§5)
   std::vector<std::vector<uint16_t>> words(n_seg);
   std::vector<std::array<uint32_t, 32>> states(n_seg);
   for (uint64_t s = 0; s < n_seg; ++s) {

@@ -56,6 +56,14 @@ def test_worked_example():
     assert gpu_decode_all(arc).tobytes() == bytes.fromhex(meta["output"][0])
 
 
+def test_renorm_order_example():
+    """Hand-derived archive in which two lanes renormalise in one step: the
+    words go to the lanes in ascending lane order."""
+    from conftest import load_hex_fixture
+    arc, meta = load_hex_fixture("renorm_order_archive.txt")
+    assert gpu_decode_all(arc).tobytes() == bytes.fromhex(meta["output"][0])
+
+
 @pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 255, 16383, 16384, 16385, 100_003])
 def test_sizes_and_ragged_tails(n):
     d = synth.random_bytes(3, n, n, b"ACGT")

@@ -1,7 +1,7 @@
 """Host-side checks of libaceapex.so that need no GPU: the library builds and
 exports every entry point declared in include/aceapex.h; its encoder's
 archives decode exactly under the oracle (an independent implementation of
-FORMAT.md); archive validation rejects damaged headers before any device
+the archive format); archive validation rejects damaged headers before any device
 work."""
 import ctypes
 import os

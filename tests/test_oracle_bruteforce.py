@@ -1,7 +1,7 @@
 """Brute-force pins of the oracle on tiny inputs (n <= 10, alphabets {a,b}
 and {A,C,G,T}, block sizes 4 and 8, min_match 2).
 
-* Every legal command list (FORMAT.md §2: lengths, non-overlap, matches kept
+* Every legal command list (the format's command rules: lengths, non-overlap, matches kept
   inside their segment) is enumerated, serialized and decoded; each must
   reproduce the input byte for byte. This exercises every way commands,
   literals, intra-segment chains and cross-segment sources can combine.

@@ -36,12 +36,36 @@ def test_worked_example_serializer_bytes():
 
 
 def test_worked_example_state_arithmetic():
-    """Lane states of the example follow from one rANS step (FORMAT.md §4)."""
+    """Lane states of the example follow from one rANS step (the format's rANS coding)."""
     rc, cmds, sym, states = oracle.segment_info(load_hex_fixture("abab_archive.txt")[0], 0)
     assert rc == oracle.OK
     assert list(sym) == [2, 0, 0, 0, 0, 0, 2, 0, 0, 0, 65, 66]
     assert [(c["lit_len"], c["mlen"], c["src"]) for c in cmds] == [(2, 2, 0), (0, 4, 0)]
     assert all(s == 65536 for s in states)
+
+
+def test_renorm_order_example_decodes():
+    """Second hand-derived archive: lanes 0 and 2 renormalise in the same step
+    and take their words in ascending lane order (fixture comments)."""
+    arc, meta = load_hex_fixture("renorm_order_archive.txt")
+    want = bytes.fromhex(meta["output"][0])
+    assert bytes(oracle.decode(arc)) == want
+    rc, cmds, sym, states = oracle.segment_info(arc, 0)
+    assert rc == oracle.OK and len(cmds) == 0
+    assert bytes(sym) == want
+    assert all(s == 65536 for s in states)
+
+
+def test_renorm_order_example_discriminates_word_order():
+    """With the two words swapped (what a descending-lane decoder would read)
+    the archive still passes the final-state check but decodes differently,
+    so the fixture pins the order and not only the states."""
+    arc, meta = load_hex_fixture("renorm_order_archive.txt")
+    swapped = arc.copy()
+    swapped[2352:2356] = [0xFF, 0x0F, 0xFE, 0x0F]
+    out = bytes(oracle.decode(swapped))
+    want = bytes.fromhex(meta["output"][0])
+    assert out != want and out[32] == ord("Y") and out[34] == ord("X") and out[:32] == want[:32]
 
 
 # ------------------------------------------------------------------------ CRC

@@ -55,3 +55,67 @@ def test_no_alloc_rejects_oversized_archive():
     small = torch.empty(10, dtype=torch.uint8, device="cuda")
     arc2 = ace.encode(synth.tiny_fastq(), min_match=16)
     assert ace.decode_all_noalloc(torch.from_numpy(arc2).to("cuda"), arc2.size, small, status) == ace.ERANGE
+
+
+def _patched(arc, edits):
+    a = arc.copy()
+    for off, dtype, value in edits:
+        a[off: off + np.dtype(dtype).itemsize] = np.frombuffer(np.array([value], dtype=dtype).tobytes(), np.uint8)
+    return a
+
+
+# Byte offsets of the archive layout: tables at 128 (four classes of 256 u16,
+# the literal class last), the directory at 2176 (24 bytes per segment:
+# payload offset u64, word count u32, command count u32, literal count u32,
+# level u16).
+_DIR = 2176
+
+
+@pytest.mark.parametrize("what", ["table_sum", "symbol_count", "level", "payload_offset"])
+def test_no_alloc_reports_corrupt_directory_on_the_device(what):
+    """The directory and tables are not checked on the host by this entry
+    point: the device rejects a bad record before touching memory through it,
+    and the status word says ECORRUPT."""
+    data = synth.pe_fastq(1 << 20, ref_len=200_000)
+    arc = ace.encode(data, min_match=16)
+    s = 5  # a segment in the middle
+    rec = _DIR + 24 * s
+    if what == "table_sum":
+        lit = 128 + 3 * 512
+        present = int(np.nonzero(arc[lit: lit + 512].view(np.uint16))[0][0])
+        bad = _patched(arc, [(lit + 2 * present, np.uint16, int(arc[lit: lit + 512].view(np.uint16)[present]) + 1)])
+    elif what == "symbol_count":
+        bad = _patched(arc, [(rec + 12, np.uint32, 5000)])      # 5000 commands: more than 16,384 symbols
+    elif what == "level":
+        bad = _patched(arc, [(rec + 20, np.uint16, int(arc[30]) + 1)])  # above the archive's level cap
+    else:
+        payload_bytes = int(arc[112:120].view(np.uint64)[0])
+        bad = _patched(arc, [(rec, np.uint64, payload_bytes - 64)])  # 16-byte aligned, but no room for the states
+    d_arc = torch.from_numpy(bad).to("cuda")
+    out = torch.empty(data.size, dtype=torch.uint8, device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    assert ace.decode_all_noalloc(d_arc, bad.size, out, status) == ace.OK
+    torch.cuda.synchronize()
+    assert int(status.item()) == ace.ECORRUPT
+    # the shared scratch is still good for the next call
+    good = torch.from_numpy(arc).to("cuda")
+    status.fill_(-1)
+    assert ace.decode_all_noalloc(good, arc.size, out, status) == ace.OK
+    torch.cuda.synchronize()
+    assert int(status.item()) == ace.OK
+    assert np.array_equal(out.cpu().numpy(), data)
+
+
+def test_no_alloc_rejects_unpadded_payload_on_the_host():
+    """A payload section whose length is not a multiple of 16 bytes would let
+    the last 16-byte copy of a segment's words read past the archive: the
+    header check rejects it before anything is queued."""
+    arc = ace.encode(synth.tiny_fastq(), min_match=16)
+    payload_bytes = int(arc[112:120].view(np.uint64)[0])
+    total = int(arc[120:128].view(np.uint64)[0])
+    bad = np.concatenate([_patched(arc, [(112, np.uint64, payload_bytes + 8), (120, np.uint64, total + 8)]),
+                          np.zeros(8, np.uint8)])
+    d_arc = torch.from_numpy(bad).to("cuda")
+    out = torch.empty(arc.size * 8, dtype=torch.uint8, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert ace.decode_all_noalloc(d_arc, bad.size, out, status) == ace.ECORRUPT
