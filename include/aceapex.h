@@ -131,6 +131,18 @@ int aceapex_decode_range(aceapex_archive *a, uint64_t byte_lo, uint64_t byte_hi,
 int aceapex_read_lookup(const aceapex_archive *a, uint64_t read_id, uint64_t *byte_lo, uint64_t *byte_hi);
 
 /*
+ * Closure of a range (paper §4 and §4.1: a range or read decodes the blocks
+ * that hold it plus the transitive closure of their source blocks): the
+ * number of segments that aceapex_decode_range(a, lo, hi, ...) decodes, in
+ * *n_segments, and the deepest dependency level among them, in *max_level
+ * (may be NULL); the wavefront of that decode has *max_level + 1 steps. Host
+ * only, no GPU work; uses the handle's closure scratch, so calls on one
+ * handle must not run concurrently. Errors: EINVAL (NULL a or n_segments),
+ * ERANGE (lo > hi or hi > N).
+ */
+int aceapex_range_closure(aceapex_archive *a, uint64_t lo, uint64_t hi, uint64_t *n_segments, uint32_t *max_level);
+
+/*
  * Report the device error word of the handle and clear it. sync != 0 first
  * synchronises `stream` (or the device when stream is NULL) so the word
  * covers every call issued before. Returns ACEAPEX_OK, ECORRUPT, ETIMEOUT or
@@ -228,6 +240,20 @@ void aceapex_server_destroy(aceapex_server *s);
 int aceapex_server_submit(aceapex_server *s, int arc, uint64_t byte_lo, uint64_t byte_hi, void *d_dst, uint64_t cap,
                           uint64_t *ticket);
 int aceapex_server_poll(aceapex_server *s, uint64_t ticket, int wait, int *done, double *latency_ms);
+/*
+ * Open-loop arrivals from native code: submits request i (archive arc[i],
+ * bytes [lo[i], hi[i]) into d_dst[i], cap[i] bytes) gap_ns[i] nanoseconds
+ * after the due time of request i - 1 (the first after gap_ns[0]), waiting on
+ * the host clock and never on completions, so a trace of Poisson gaps is
+ * offered at its own rate whatever the serving latency. status[i] receives
+ * the aceapex_server_submit result and ticket[i] its ticket (0 when refused);
+ * *submit_seconds (may be NULL) the time from the call to the last
+ * submission. Tickets are then polled as usual. Errors: EINVAL (NULL server
+ * or arrays).
+ */
+int aceapex_server_replay(aceapex_server *s, uint64_t n, const int *arc, const uint64_t *lo, const uint64_t *hi,
+                          void *const *d_dst, const uint64_t *cap, const uint64_t *gap_ns, uint64_t *ticket,
+                          int *status, double *submit_seconds);
 int aceapex_server_get_stats(aceapex_server *s, aceapex_server_stats *out);
 
 /*

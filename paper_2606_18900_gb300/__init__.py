@@ -138,6 +138,8 @@ def lib():
             L.aceapex_decode_all.argtypes = [vp, vp, u64, vp, ctypes.POINTER(Stats)]
             L.aceapex_decode_range.argtypes = [vp, u64, u64, vp, u64, vp]
             L.aceapex_read_lookup.argtypes = [vp, u64, u64p, u64p]
+            L.aceapex_range_closure.argtypes = [vp, u64, u64, u64p, ctypes.POINTER(ctypes.c_uint32)]
+            L.aceapex_range_closure.restype = i32
             L.aceapex_last_error.argtypes = [vp, i32, vp]
             L.aceapex_set_wait_limit.argtypes = [vp, u64]
             L.aceapex_debug_block_segments.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), u32]
@@ -158,6 +160,9 @@ def lib():
             L.aceapex_server_poll.argtypes = [vp, u64, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]
             L.aceapex_server_poll.restype = i32
             L.aceapex_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+            L.aceapex_server_replay.argtypes = [vp, u64, ctypes.POINTER(i32), u64p, u64p, ctypes.POINTER(vp), u64p,
+                                                u64p, u64p, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]
+            L.aceapex_server_replay.restype = i32
             L.aceapex_server_get_stats.restype = i32
             L.aceapex_decode_all_noalloc.argtypes = [vp, u64, vp, u64, vp, vp]
             L.aceapex_decode_all_noalloc.restype = i32
@@ -408,6 +413,13 @@ class Archive:
         cap = out.numel() * out.element_size()
         _check(lib().aceapex_decode_range(self._h, lo, hi, _ptr(out), cap, _stream(stream)), "aceapex_decode_range")
 
+    def range_closure(self, lo: int, hi: int):
+        """(segments decoded, deepest level) of a range decode of [lo, hi)."""
+        n, lv = ctypes.c_uint64(), ctypes.c_uint32()
+        _check(lib().aceapex_range_closure(self._h, lo, hi, ctypes.byref(n), ctypes.byref(lv)),
+               "aceapex_range_closure")
+        return n.value, lv.value
+
     def read_lookup(self, read_id: int):
         lo, hi = ctypes.c_uint64(), ctypes.c_uint64()
         _check(lib().aceapex_read_lookup(self._h, read_id, ctypes.byref(lo), ctypes.byref(hi)), "aceapex_read_lookup")
@@ -475,6 +487,25 @@ class Server:
         _check(lib().aceapex_server_submit(self._h, arc, lo, hi, _ptr(out), out.numel() * out.element_size(),
                                            ctypes.byref(t)), "aceapex_server_submit")
         return t.value
+
+    def replay(self, reqs, outs, gaps_ns):
+        """Offer requests [(arc, lo, hi), ...] into device tensors `outs` with
+        the given inter-arrival gaps (ns) from the library's own thread
+        (aceapex_server_replay). Returns (tickets, status codes, seconds from
+        the call to the last submission); a refused request has ticket 0."""
+        n = len(reqs)
+        arc = (ctypes.c_int * n)(*[r[0] for r in reqs])
+        lo = (ctypes.c_uint64 * n)(*[r[1] for r in reqs])
+        hi = (ctypes.c_uint64 * n)(*[r[2] for r in reqs])
+        dst = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
+        cap = (ctypes.c_uint64 * n)(*[o.numel() * o.element_size() for o in outs])
+        gap = (ctypes.c_uint64 * n)(*[int(g) for g in gaps_ns])
+        tk = (ctypes.c_uint64 * n)()
+        stt = (ctypes.c_int * n)()
+        secs = ctypes.c_double()
+        _check(lib().aceapex_server_replay(self._h, n, arc, lo, hi, dst, cap, gap, tk, stt, ctypes.byref(secs)),
+               "aceapex_server_replay")
+        return list(tk), list(stt), secs.value
 
     def poll(self, ticket: int, wait: bool = False):
         """None while pending; else the latency in ms (raises on a failed request)."""

@@ -136,6 +136,12 @@ struct aceapex_archive {
   Staging stage_work;
   std::vector<uint32_t> mark;
   uint32_t mark_gen = 0;
+  // device closures (wide dependency lists): the lists on the device, tagged
+  // marks, the member list, counters, and a pinned word for the member count
+  DBuf<uint64_t> d_dep_ptr;
+  DBuf<uint32_t> d_deps, d_cmark, d_clist, d_ccnt;
+  Staging stage_cnt;
+  uint32_t cgen = 0;
 
   // ring streaming
   DBuf<uint8_t> d_ring;
@@ -184,6 +190,8 @@ struct aceapex_archive {
     d_work.release(); d_ring.release(); d_seg_crc.release(); d_batch_arcs.release(); d_batch_views.release();
     d_fq_streams.release(); d_fq_counts.release(); d_fq_nl.release(); d_fq_offs.release();
     d_host_out.release(); d_win_work.release();
+    d_dep_ptr.release(); d_deps.release(); d_cmark.release(); d_clist.release(); d_ccnt.release();
+    stage_cnt.release();
     for (cudaEvent_t e : win_ev) cudaEventDestroy(e);
     win_ev.clear();
     if (copy_st) cudaStreamDestroy(copy_st);
@@ -204,8 +212,10 @@ int ensure_scratch(aceapex_archive *A);
 // a DecodeLaunch with the handle's control words, scratch and knobs
 DecodeLaunch base_launch(aceapex_archive *A);
 OutView linear_view(uint8_t *base, uint64_t origin);
-// transitive source closure of segments [s_lo, s_hi] from the stored lists
-void closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, std::vector<uint32_t> &out);
+// transitive source closure of segments [s_lo, s_hi] from the stored lists;
+// with max_edges > 0, gives up (returns false) after visiting that many
+// dependency entries
+bool closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, std::vector<uint32_t> &out, uint64_t max_edges = 0);
 // the same for a list of seed segments; marks with a fresh generation of A->mark
 void closure_of(aceapex_archive *A, const uint32_t *seeds, uint64_t n, std::vector<uint32_t> &out);
 

@@ -269,7 +269,7 @@ OutView linear_view(uint8_t *base, uint64_t origin) {
 }
 
 // transitive source closure of segments [s_lo, s_hi] (host, from the stored lists)
-void closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, std::vector<uint32_t> &out) {
+bool closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, std::vector<uint32_t> &out, uint64_t max_edges) {
   if (A->mark.size() != A->h.n_seg) A->mark.assign(A->h.n_seg, 0);
   if (++A->mark_gen == 0) {
     std::fill(A->mark.begin(), A->mark.end(), 0);
@@ -283,10 +283,13 @@ void closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, std::vector<uint3
       A->mark[s] = g;
       stack.push_back((uint32_t)s);
     }
+  uint64_t edges = 0;
   while (!stack.empty()) {
     uint32_t s = stack.back();
     stack.pop_back();
     out.push_back(s);
+    edges += A->dep_ptr[s + 1] - A->dep_ptr[s];
+    if (max_edges && edges > max_edges) return false;
     for (uint64_t i = A->dep_ptr[s]; i < A->dep_ptr[s + 1]; ++i) {
       uint32_t d = A->deps[i];
       if (A->mark[d] != g) {
@@ -295,6 +298,7 @@ void closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, std::vector<uint3
       }
     }
   }
+  return true;
 }
 
 void closure_of(aceapex_archive *A, const uint32_t *seeds, uint64_t n, std::vector<uint32_t> &out) {
@@ -325,18 +329,85 @@ void closure_of(aceapex_archive *A, const uint32_t *seeds, uint64_t n, std::vect
   }
 }
 
+// Host walks stop after this many dependency entries (tens of microseconds);
+// wider closures are found on the device.
+constexpr uint64_t kHostClosureEdges = 16384;
+
+// The closure of [s_lo, s_hi] found on the device: the lists are uploaded on
+// first use; the members of each level from the seeds' deepest level down to 1
+// add their dependencies, then the members are sorted by level into d_work
+// with their page-table slots. The member count comes back to the host (one
+// stream synchronisation) so that the arena can be sized for it.
+int device_closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, cudaStream_t st, uint32_t *n_out) {
+  const uint64_t ns = A->h.n_seg;
+  if (!A->d_dep_ptr.p) {
+    if (A->d_dep_ptr.alloc(ns + 1) != cudaSuccess || A->d_deps.alloc(std::max<uint64_t>(A->h.n_deps, 1)) != cudaSuccess ||
+        A->d_cmark.alloc(ns) != cudaSuccess || A->d_clist.alloc(ns) != cudaSuccess ||
+        A->d_ccnt.alloc(4) != cudaSuccess || A->stage_cnt.reserve(16) != cudaSuccess)
+      return ACEAPEX_ENOMEM;
+    if (cudaMemcpy(A->d_dep_ptr.p, A->dep_ptr.data(), 8 * (ns + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (A->h.n_deps &&
+         cudaMemcpy(A->d_deps.p, A->deps.data(), 4 * A->h.n_deps, cudaMemcpyHostToDevice) != cudaSuccess) ||
+        cudaMemset(A->d_cmark.p, 0, 4 * ns) != cudaSuccess)
+      return ACEAPEX_ECUDA;
+    A->cgen = 0;
+  }
+  if (A->d_work.n < ns) {
+    cudaStreamSynchronize(st);
+    if (A->d_work.alloc(ns) != cudaSuccess) return ACEAPEX_ENOMEM;
+  }
+  if (++A->cgen == 0) {  // tags wrapped: clear the marks
+    if (cudaMemsetAsync(A->d_cmark.p, 0, 4 * ns, st) != cudaSuccess) return ACEAPEX_ECUDA;
+    A->cgen = 1;
+  }
+  ClosureDev C{A->d_dep_ptr.p, A->d_deps.p, A->d_dir.p, A->d_cmark.p, A->d_clist.p, A->d_ccnt.p};
+  uint32_t top = 0;
+  for (uint64_t s = s_lo; s <= s_hi; ++s) top = std::max<uint32_t>(top, A->dir[s].level);
+  cudaError_t e = launch_closure_seed(C, (uint32_t)s_lo, (uint32_t)(s_hi - s_lo + 1), A->cgen, st);
+  for (uint32_t l = top; e == cudaSuccess && l >= 1; --l) e = launch_closure_expand(C, l, A->cgen, st);
+  if (e == cudaSuccess) e = launch_closure_order(C, A->d_work.p, A->d_page.p, A->d_ccnt.p + 1, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(A->stage_cnt.p, A->d_ccnt.p + 1, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return ACEAPEX_ECUDA;
+  *n_out = *static_cast<const uint32_t *>(A->stage_cnt.p);
+  return *n_out <= ns ? ACEAPEX_OK : ACEAPEX_ECUDA;
+}
+
 // decode the closure of [s_lo, s_hi] into arena slots (paged view); returns the view
 int decode_closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, cudaStream_t st, OutView *view_out,
                    uint32_t *n_out, bool begin) {
-  std::vector<uint32_t> segs;
-  closure(A, s_lo, s_hi, segs);
-  std::vector<WorkItem> work;
-  level_order(A->dir, segs.data(), segs.size(), 0, work);
   const uint64_t S = uint64_t(1) << A->h.log2_S;
   if (!A->d_page.p) {
     if (A->d_page.alloc(A->h.n_seg) != cudaSuccess) return ACEAPEX_ENOMEM;
     if (cudaMemsetAsync(A->d_page.p, 0xFF, 4 * A->h.n_seg, st) != cudaSuccess) return ACEAPEX_ECUDA;
   }
+  std::vector<uint32_t> segs;
+  if (!closure(A, s_lo, s_hi, segs, kHostClosureEdges)) {
+    uint32_t n = 0;
+    int rc = device_closure(A, s_lo, s_hi, st, &n);
+    if (rc) return rc;
+    if (A->d_arena.n < n * S) {
+      cudaStreamSynchronize(st);
+      if (A->d_arena.alloc(std::max<uint64_t>(n, 64) * S) != cudaSuccess) return ACEAPEX_ENOMEM;
+    }
+    uint32_t *ge = global_epoch(A->device);
+    if (!ge) return ACEAPEX_ECUDA;
+    cudaError_t e = begin ? launch_begin(ge, A->epoch(), A->counter(), st) : cudaMemsetAsync(A->counter(), 0, 4, st);
+    if (e != cudaSuccess) return ACEAPEX_ECUDA;
+    DecodeLaunch L = base_launch(A);
+    OutView v{};
+    v.page = A->d_page.p;
+    v.slot_base = A->d_arena.p;
+    L.view0 = v;
+    L.work = A->d_work.p;
+    L.n_work = n;
+    if ((e = launch_decode(L, A->grid, kBlock, st)) != cudaSuccess) return ACEAPEX_ECUDA;
+    *view_out = v;
+    *n_out = n;
+    return ACEAPEX_OK;
+  }
+  std::vector<WorkItem> work;
+  level_order(A->dir, segs.data(), segs.size(), 0, work);
   if (A->d_arena.n < work.size() * S) {
     cudaStreamSynchronize(st);
     uint64_t slots = std::max<uint64_t>(work.size(), 64);
@@ -573,6 +644,21 @@ int aceapex_decode_range(aceapex_archive *a, uint64_t lo, uint64_t hi, void *d_o
   cudaError_t e = launch_gather(v, a->h.log2_S, lo, hi, static_cast<uint8_t *>(d_out), st);
   if (e == cudaSuccess) e = launch_clear_pages(a->d_page.p, a->d_work.p, n, st);
   return cuda_status(e);
+}
+
+int aceapex_range_closure(aceapex_archive *a, uint64_t lo, uint64_t hi, uint64_t *n_segments, uint32_t *max_level) {
+  if (!a || !n_segments) return ACEAPEX_EINVAL;
+  if (lo > hi || hi > a->h.n) return ACEAPEX_ERANGE;
+  *n_segments = 0;
+  if (max_level) *max_level = 0;
+  if (hi == lo) return ACEAPEX_OK;
+  std::vector<uint32_t> segs;
+  closure(a, lo >> a->h.log2_S, (hi - 1) >> a->h.log2_S, segs);
+  uint32_t lv = 0;
+  for (uint32_t s : segs) lv = std::max<uint32_t>(lv, a->dir[s].level);
+  *n_segments = segs.size();
+  if (max_level) *max_level = lv;
+  return ACEAPEX_OK;
 }
 
 int aceapex_read_lookup(const aceapex_archive *a, uint64_t read_id, uint64_t *byte_lo, uint64_t *byte_hi) {

@@ -222,8 +222,13 @@ struct Stage {
 #ifdef ACEAPEX_PHASE_CLOCKS
 // Warp-cycle counters per phase (instrumented build only): 0 command-class
 // rANS, 1 command parse, 2 literal rANS and placement, 3 dependency waits,
-// 4 match copies, 5 the rest of the work loop.
-__device__ unsigned long long g_phase_cycles[8];
+// 4 match copies, 5 the rest of the work loop; then event counts: 6 match
+// chunks, 7 copy rounds, 8 copy units, 9 segments.
+__device__ unsigned long long g_phase_cycles[16];
+#define PHASE_COUNT(i, v) \
+  do {                    \
+    if (lane == 0) ph[i] += (v); \
+  } while (0)
 #define PHASE_MARK(i)                    \
   do {                                   \
     if (lane == 0) {                     \
@@ -235,6 +240,9 @@ __device__ unsigned long long g_phase_cycles[8];
 #else
 #define PHASE_MARK(i) \
   do {                \
+  } while (0)
+#define PHASE_COUNT(i, v) \
+  do {                    \
   } while (0)
 #endif
 
@@ -432,13 +440,19 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
       K0 += 32;
     }
     for (; t0 + 128 <= n_sym; t0 += 128) {
+      if (E - K0 >= 128) {  // no run ends inside these four steps
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        uint32_t dq = 0;
-        const bool hb = bound(dq);
-        p[32 * u] = (uint8_t)lit_rans();
-        if (hb) p += dq;
-        K0 += 32;
+        for (int u = 0; u < 4; ++u) p[32 * u] = (uint8_t)lit_rans();
+        K0 += 128;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          uint32_t dq = 0;
+          const bool hb = bound(dq);
+          p[32 * u] = (uint8_t)lit_rans();
+          if (hb) p += dq;
+          K0 += 32;
+        }
       }
       p += 128;
       advance();
@@ -516,6 +530,7 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
       break;
     }
     PHASE_MARK(3);
+    PHASE_COUNT(6, 1);
     mt->src[lane] = src;
     mt->dst[lane] = dst;
     __syncwarp();
@@ -561,6 +576,8 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
       const uint32_t nu = !ready ? 0 : vec ? (((uint32_t)(dst - seg_start) & 15u) + ml + 15) >> 4 : (ml + 15) >> 4;
       const uint32_t incl = warp_incl_scan(nu, lane);
       const uint32_t total = __shfl_sync(kFull, incl, 31);
+      PHASE_COUNT(7, 1);
+      PHASE_COUNT(8, total);
       mt->start[lane] = incl - nu;
       mt->len[lane] = ml;
       if (lane == 31) mt->start[32] = incl;
@@ -628,6 +645,7 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
   }
   if (!ok && lane == 0 && ld_relaxed(L.err) == 0) latch(L.err, kErrCorrupt);
 
+  PHASE_COUNT(9, 1);
   // ------------------------------------------------------------- publish
   __threadfence();
   __syncwarp();
@@ -670,12 +688,12 @@ __device__ __forceinline__ WarpSmem warp_smem(uint8_t *smem, int wid) {
 
 #ifdef ACEAPEX_PHASE_CLOCKS
 #define PHASE_DECL        \
-  uint64_t ph[6] = {};    \
+  uint64_t ph[10] = {};   \
   uint64_t ph_t = clock64()
-#define PHASE_FLUSH()                                                                              \
-  do {                                                                                             \
-    if (lane == 0)                                                                                 \
-      for (int i_ = 0; i_ < 6; ++i_) atomicAdd(&g_phase_cycles[i_], (unsigned long long)ph[i_]); \
+#define PHASE_FLUSH()                                                                               \
+  do {                                                                                              \
+    if (lane == 0)                                                                                  \
+      for (int i_ = 0; i_ < 10; ++i_) atomicAdd(&g_phase_cycles[i_], (unsigned long long)ph[i_]); \
   } while (0)
 #else
 #define PHASE_DECL            \
@@ -820,6 +838,76 @@ __global__ void multi_gather_kernel(const GatherJob *jobs, uint32_t n_jobs, uint
 __global__ void set_pages_kernel(uint32_t *page, const WorkItem *work, uint32_t n) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) page[work[i].seg] = i;
+}
+
+// -------------------------------------------------------- device closures
+__global__ void closure_seed_kernel(ClosureDev C, uint32_t s_lo, uint32_t n, uint32_t gen) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    C.mark[s_lo + i] = gen;
+    C.list[i] = s_lo + i;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *C.cnt = n;
+}
+
+// One warp per member of the given level (grid-stride over the list); its
+// lanes walk the member's dependency list. A dependency joins the closure
+// when this warp is the first to tag it with gen; the warp reserves the list
+// slots of its new members with one atomic. Members added here have lower
+// levels, so the entries a warp sees beyond its first reading of cnt are
+// skipped by the level test.
+__global__ void closure_expand_kernel(ClosureDev C, uint32_t level, uint32_t gen) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  const uint32_t n = ld_relaxed(C.cnt);
+  for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+    const uint32_t s = C.list[i];
+    if (C.dir[s].level != level) continue;
+    const uint64_t b = C.dep_ptr[s], e = C.dep_ptr[s + 1];
+    for (uint64_t k0 = b; k0 < e; k0 += 32) {
+      const uint64_t k = k0 + lane;
+      uint32_t d = 0;
+      bool fresh = false;
+      if (k < e) {
+        d = C.deps[k];
+        fresh = atomicExch(C.mark + d, gen) != gen;
+      }
+      const uint32_t m = __ballot_sync(kFull, fresh);
+      if (!m) continue;
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(C.cnt, (uint32_t)__popc(m));
+      base = __shfl_sync(kFull, base, 0);
+      if (fresh) C.list[base + __popc(m & lanemask_lt())] = d;
+    }
+  }
+}
+
+// one CTA: counting sort of the members by level (levels < 65536)
+constexpr int kClosureLevels = 256;
+__global__ void __launch_bounds__(1024) closure_order_kernel(ClosureDev C, WorkItem *work, uint32_t *page,
+                                                             uint32_t *n_out) {
+  __shared__ uint32_t off[kClosureLevels];
+  const uint32_t n = *C.cnt;
+  for (int l = threadIdx.x; l < kClosureLevels; l += blockDim.x) off[l] = 0;
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
+    atomicAdd(&off[min((uint32_t)C.dir[C.list[i]].level, (uint32_t)(kClosureLevels - 1))], 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int l = 0; l < kClosureLevels; ++l) {
+      const uint32_t c = off[l];
+      off[l] = run;
+      run += c;
+    }
+    *n_out = n;
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint32_t s = C.list[i];
+    const uint32_t pos = atomicAdd(&off[min((uint32_t)C.dir[s].level, (uint32_t)(kClosureLevels - 1))], 1u);
+    work[pos] = WorkItem{0u, s};
+    page[s] = pos;
+  }
 }
 
 // ------------------------------------------------------------------- CRC-32
@@ -1189,6 +1277,24 @@ cudaError_t launch_set_pages(uint32_t *page, const WorkItem *work, uint32_t n, c
   return cudaGetLastError();
 }
 
+cudaError_t launch_closure_seed(ClosureDev C, uint32_t s_lo, uint32_t n, uint32_t gen, cudaStream_t st) {
+  closure_seed_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, st>>>(C, s_lo, n, gen);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_closure_expand(ClosureDev C, uint32_t level, uint32_t gen, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  closure_expand_kernel<<<2 * sms, 512, 0, st>>>(C, level, gen);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_closure_order(ClosureDev C, WorkItem *work, uint32_t *page, uint32_t *n_out, cudaStream_t st) {
+  closure_order_kernel<<<1, 1024, 0, st>>>(C, work, page, n_out);
+  return cudaGetLastError();
+}
+
 static bool g_crc_ready[64] = {};
 
 // Fills g_crc_tabs on the current device (once per device).
@@ -1456,17 +1562,18 @@ extern "C" int aceapex_decode_all_noalloc(const void *d_archive, uint64_t nbytes
 #ifdef ACEAPEX_PHASE_CLOCKS
 // Instrumented build only: copies the warp cycles that the decode kernels
 // spent in each phase (command-class rANS, command parse, literal rANS and
-// placement, dependency waits, match copies, the rest of the work loop) since
-// the last reset into out[0 .. n) (n <= 6), and zeroes them when reset != 0.
+// placement, dependency waits, match copies, the rest of the work loop) and
+// the event counts (match chunks, copy rounds, copy units, segments) since
+// the last reset into out[0 .. n) (n <= 10), and zeroes them when reset != 0.
 // Synchronises the current device. Returns 0, or 4 on a CUDA error.
 extern "C" int aceapex_phase_cycles(uint64_t *out, int n, int reset) {
-  unsigned long long h[8] = {};
+  unsigned long long h[16] = {};
   if (cudaDeviceSynchronize() != cudaSuccess ||
       cudaMemcpyFromSymbol(h, aceapex::g_phase_cycles, sizeof(h)) != cudaSuccess)
     return 4;
-  for (int i = 0; i < n && i < 6; ++i) out[i] = h[i];
+  for (int i = 0; i < n && i < 10; ++i) out[i] = h[i];
   if (reset) {
-    const unsigned long long z[8] = {};
+    const unsigned long long z[16] = {};
     if (cudaMemcpyToSymbol(aceapex::g_phase_cycles, z, sizeof(z)) != cudaSuccess) return 4;
   }
   return 0;

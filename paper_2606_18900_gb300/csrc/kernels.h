@@ -123,6 +123,28 @@ cudaError_t launch_fastq_interleave(const uint8_t *const base[4], const uint64_t
                                     uint64_t *offs, uint32_t *const nl[4], const uint64_t cap[4], uint32_t *err,
                                     uint8_t *out, cudaStream_t st);
 
+// Transitive source closure on the device, for range decodes whose closure
+// is too wide to walk on the host (paper §4.1: a read decodes its covering
+// blocks plus their sources). mark: one u32 per segment, equal to gen when the
+// segment is in the current closure; list: the members in discovery order;
+// cnt[0]: their number. Every dependency has a lower level than its reader, so
+// expanding the members of level L (max level down to 1) after all higher
+// levels visits each member once.
+struct ClosureDev {
+  const uint64_t *dep_ptr;
+  const uint32_t *deps;
+  const SegRec *dir;
+  uint32_t *mark;
+  uint32_t *list;
+  uint32_t *cnt;
+};
+// members := segments [s_lo, s_lo + n)
+cudaError_t launch_closure_seed(ClosureDev C, uint32_t s_lo, uint32_t n, uint32_t gen, cudaStream_t st);
+// add the unmarked dependencies of every member of level `level`
+cudaError_t launch_closure_expand(ClosureDev C, uint32_t level, uint32_t gen, cudaStream_t st);
+// members sorted by level into work[0 .. n), page[seg] = its position, n into *n_out
+cudaError_t launch_closure_order(ClosureDev C, WorkItem *work, uint32_t *page, uint32_t *n_out, cudaStream_t st);
+
 // CRC-32 of each window [lo + k*window, ...) of the ring view, written to crc[k].
 cudaError_t launch_window_crc(OutView v, uint64_t lo, uint64_t hi, uint64_t window, uint32_t *crc, uint32_t *seg_crc,
                               uint32_t log2_S, cudaStream_t st);

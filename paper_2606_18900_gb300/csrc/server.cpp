@@ -361,6 +361,25 @@ int aceapex_server_submit(aceapex_server *S, int arc, uint64_t lo, uint64_t hi, 
   return ACEAPEX_OK;
 }
 
+int aceapex_server_replay(aceapex_server *S, uint64_t n, const int *arc, const uint64_t *lo, const uint64_t *hi,
+                          void *const *d_dst, const uint64_t *cap, const uint64_t *gap_ns, uint64_t *ticket,
+                          int *status, double *submit_seconds) {
+  if (!S || (n && (!arc || !lo || !hi || !d_dst || !cap || !gap_ns || !ticket || !status))) return ACEAPEX_EINVAL;
+  const auto t0 = std::chrono::steady_clock::now();
+  auto due = t0;
+  for (uint64_t i = 0; i < n; ++i) {
+    due += std::chrono::nanoseconds(gap_ns[i]);
+    while (std::chrono::steady_clock::now() < due) {
+    }
+    ticket[i] = 0;
+    status[i] = aceapex_server_submit(S, arc[i], lo[i], hi[i], d_dst[i], cap[i], ticket + i);
+    if (status[i] != ACEAPEX_OK) ticket[i] = 0;
+  }
+  if (submit_seconds)
+    *submit_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return ACEAPEX_OK;
+}
+
 int aceapex_server_poll(aceapex_server *S, uint64_t ticket, int wait, int *done, double *latency_ms) {
   if (!S || !done) return ACEAPEX_EINVAL;
   std::unique_lock<std::mutex> lk(S->mu);

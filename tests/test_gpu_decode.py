@@ -408,3 +408,45 @@ def test_batch_graph_replay_and_autotune(tmp_path):
             assert_same(o.cpu().numpy(), x)
     for a in arcs:
         a.close()
+
+
+def _closure_edges(sec, lo, hi):
+    """Dependency entries a host walk of [lo, hi)'s closure visits."""
+    dp, deps, lS = sec["dep_ptr"], sec["deps"], sec["log2_S"]
+    seen = set(range(lo >> lS, ((hi - 1) >> lS) + 1))
+    stack, edges = list(seen), 0
+    while stack:
+        s = stack.pop()
+        edges += int(dp[s + 1] - dp[s])
+        for d in deps[dp[s]:dp[s + 1]]:
+            if int(d) not in seen:
+                seen.add(int(d))
+                stack.append(int(d))
+    return edges, len(seen)
+
+
+def test_range_decode_with_wide_closures():
+    """Reads of a paired-end FASTQ whose segments each draw on about a hundred
+    earlier segments: closures too wide for the host walk (more than 16,384
+    dependency entries) are found on the device. Every read and range equals
+    the source, and the closure query agrees with a walk in Python."""
+    data = synth.pe_fastq(32 << 20, ref_len=5_000_000)
+    arc = ace.encode(data, min_match=16, reads=ace.fastq_index(data))
+    sec = oracle.sections(arc)
+    wide = 0
+    with ace.Archive(arc) as a:
+        n_reads = a.stats()["n_reads"]
+        buf = torch.empty(2 << 20, dtype=torch.uint8, device="cuda")
+        ranges = [a.read_lookup(int(r)) for r in synth.uniform(9, 1, 16, n_reads)]
+        starts = synth.uniform(9, 2, 6, data.size // 2)
+        ranges += [(data.size // 2 + int(s), min(data.size, data.size // 2 + int(s) + (1 << 20))) for s in starts]
+        ranges += [(data.size - (1 << 20), data.size), (data.size // 2, data.size // 2 + 3), (0, 100)]
+        for lo, hi in ranges:
+            edges, nseg = _closure_edges(sec, lo, hi)
+            wide += edges > 16384
+            assert a.range_closure(lo, hi)[0] == nseg
+            buf.fill_(0)
+            a.decode_range(lo, hi, buf)
+            a.check()
+            assert bytes(buf[: hi - lo].cpu().numpy()) == data[lo:hi].tobytes(), (lo, hi)
+    assert wide >= 3
