@@ -278,7 +278,7 @@ def random_reads(arc, data, n, seed, stream, device):
 
 
 PHASES = ("cmd_rans", "parse", "lit_rans", "waits", "copies", "loop")
-COUNTS = ("chunks", "rounds", "units", "segments")
+COUNTS = ("chunks", "rounds", "units", "segments", "waited_chunks")
 
 
 def phase_child(args):
@@ -295,25 +295,25 @@ def phase_child(args):
     L = ace.lib()
     L.aceapex_phase_cycles.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
     L.aceapex_phase_cycles.restype = ctypes.c_int
-    buf = (ctypes.c_uint64 * 10)()
+    buf = (ctypes.c_uint64 * 11)()
     with ace.Archive(arc_bytes) as a:
         out = torch.empty(a.size, dtype=torch.uint8, device="cuda")
         stream = torch.cuda.Stream()
         for _ in range(2):
             a.decode_all(out, stream)
         a.check(stream)
-        if L.aceapex_phase_cycles(buf, 10, 1):
+        if L.aceapex_phase_cycles(buf, 11, 1):
             raise SystemExit("phase counters unavailable")
         reps = 5
         for _ in range(reps):
             a.decode_all(out, stream)
         a.check(stream)
-        if L.aceapex_phase_cycles(buf, 10, 1):
+        if L.aceapex_phase_cycles(buf, 11, 1):
             raise SystemExit("phase counters unavailable")
     cyc = [int(v) for v in buf[:6]]
     tot = sum(cyc)
     print(json.dumps({"share": {k: v / tot for k, v in zip(PHASES, cyc)},
-                      "per_decode": {k: int(v) // reps for k, v in zip(COUNTS, buf[6:10])}}), flush=True)
+                      "per_decode": {k: int(v) // reps for k, v in zip(COUNTS, buf[6:11])}}), flush=True)
 
 
 def phase_split(arc_bytes, ms_decode, U):

@@ -257,6 +257,7 @@ DecodeLaunch base_launch(aceapex_archive *A) {
   L.wait_ns = A->wait_ns;
   L.active_warps = A->active_warps;
   L.stage_cap = A->stage_cap;
+  L.max_stage = A->max_cmd_syms;
   return L;
 }
 

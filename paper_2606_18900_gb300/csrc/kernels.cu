@@ -192,16 +192,29 @@ __device__ __forceinline__ void sts_u16(uint32_t a, uint32_t v) {
   asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"((uint16_t)v) : "memory");
 }
 
-// The command staging area of a warp (shared memory, or the warp's global
-// slot for segments whose command streams do not fit): byte offsets; the area
-// is 4-byte aligned.
+// The command staging area of a warp: shared memory (kShared, read and
+// written through its shared-window address), or a generic pointer to shared
+// memory or to the warp's global slot for segments whose command streams do
+// not fit. Byte offsets; the area is 4-byte aligned.
+template <bool kShared>
 struct Stage {
   uint8_t *p;
-  __device__ __forceinline__ uint32_t u16(uint32_t o) const { return *reinterpret_cast<const uint16_t *>(p + o); }
-  __device__ __forceinline__ uint32_t u32(uint32_t o) const { return *reinterpret_cast<const uint32_t *>(p + o); }
-  __device__ __forceinline__ void st8(uint32_t o, uint32_t v) const { p[o] = (uint8_t)v; }
+  uint32_t s;  // shared-window address of p (kShared)
+  __device__ __forceinline__ uint32_t u16(uint32_t o) const {
+    if (kShared) return lds_u16(s + o);
+    return *reinterpret_cast<const uint16_t *>(p + o);
+  }
+  __device__ __forceinline__ uint32_t u32(uint32_t o) const {
+    if (kShared) return lds_u32(s + o);
+    return *reinterpret_cast<const uint32_t *>(p + o);
+  }
+  __device__ __forceinline__ void st8(uint32_t o, uint32_t v) const {
+    if (kShared) asm volatile("st.shared.u8 [%0], %1;" ::"r"(s + o), "r"(v) : "memory");
+    else p[o] = (uint8_t)v;
+  }
   __device__ __forceinline__ void st16(uint32_t o, uint32_t v) const {
-    *reinterpret_cast<uint16_t *>(p + o) = (uint16_t)v;
+    if (kShared) asm volatile("st.shared.u16 [%0], %1;" ::"r"(s + o), "h"((uint16_t)v) : "memory");
+    else *reinterpret_cast<uint16_t *>(p + o) = (uint16_t)v;
   }
   // W-byte little-endian value at offset o (1 <= W <= 8); reads only the
   // aligned 4-byte words that hold bytes of [o, o + W), so never past the
@@ -223,7 +236,8 @@ struct Stage {
 // Warp-cycle counters per phase (instrumented build only): 0 command-class
 // rANS, 1 command parse, 2 literal rANS and placement, 3 dependency waits,
 // 4 match copies, 5 the rest of the work loop; then event counts: 6 match
-// chunks, 7 copy rounds, 8 copy units, 9 segments.
+// chunks, 7 copy rounds, 8 copy units, 9 segments, 10 chunks whose source
+// flags were not all set at the first reading.
 __device__ unsigned long long g_phase_cycles[16];
 #define PHASE_COUNT(i, v) \
   do {                    \
@@ -265,10 +279,10 @@ __device__ unsigned long long g_phase_cycles[16];
 // segments' flags, then match copies in rounds: a round copies every pending
 // match whose source does not overlap the output of an earlier pending match,
 // the bytes of the round spread over all lanes; (5) publish.
-template <bool kSmemLut, int kMode>
+template <bool kSmemLut, int kMode, bool kSharedStage>
 __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const DevArchive &A, const OutView &V,
                                                     uint32_t seg, uint32_t epoch, const uint32_t *lut,
-                                                    uint32_t lut_s, const Stage st, MatchTable *mt,
+                                                    uint32_t lut_s, const Stage<kSharedStage> st, MatchTable *mt,
                                                     uint32_t ring_s, int lane, const SegRec &d, uint64_t *ph,
                                                     uint64_t &ph_t) {
   (void)ph;
@@ -356,9 +370,23 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
   // wb inside blk) four steps read only those two blocks.
   uint32_t t0 = 0, pend = 0;
   if (ok) {
+    // four steps inside one class: the table row is known for all lanes
+    auto cls_step = [&](uint32_t row) -> uint32_t {
+      const uint32_t e = entry(row | (x & (kScale - 1)));
+      x = ((e >> 20) + 1u) * (x >> kScaleBits) + ((e >> 8) & 0xFFFu);
+      renorm(x < kRansL);
+      return e & 0xFFu;
+    };
     for (; t0 + 128 <= b3; t0 += 128) {
+      const uint32_t c_lo = (uint32_t)(t0 >= b1) + (uint32_t)(t0 >= b2);
+      const uint32_t c_hi = (uint32_t)(t0 + 127 >= b1) + (uint32_t)(t0 + 127 >= b2);
+      if (c_lo == c_hi) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) st.st8(t0 + 32 * u + lane, cmd_step(t0 + 32 * u + lane));
+        for (int u = 0; u < 4; ++u) st.st8(t0 + 32 * u + lane, cls_step(c_lo << kScaleBits));
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) st.st8(t0 + 32 * u + lane, cmd_step(t0 + 32 * u + lane));
+      }
       advance();
     }
     for (; t0 < b3; t0 += 32) {
@@ -523,11 +551,13 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
       ok = false;
       break;
     }
-    if (!__all_sync(kFull, f0 == epoch && f1 == epoch) &&
-        (!wait_flags(A.flags + (need0 ? q0 : 0), need0, epoch, deadline, L.err, lane) ||
-         !wait_flags(A.flags + (need1 ? q1 : 0), need1, epoch, deadline, L.err, lane))) {
-      ok = false;
-      break;
+    if (!__all_sync(kFull, f0 == epoch && f1 == epoch)) {
+      PHASE_COUNT(10, 1);
+      if (!wait_flags(A.flags + (need0 ? q0 : 0), need0, epoch, deadline, L.err, lane) ||
+          !wait_flags(A.flags + (need1 ? q1 : 0), need1, epoch, deadline, L.err, lane)) {
+        ok = false;
+        break;
+      }
     }
     PHASE_MARK(3);
     PHASE_COUNT(6, 1);
@@ -653,16 +683,21 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
 }
 
 // Decode one segment: its command streams are staged in the warp's shared
-// area when they fit (scap bytes), else in its global slot gstage.
-template <bool kSmemLut, int kMode>
+// area when they fit (scap bytes), else in its global slot gstage. With
+// kSharedStage every segment of the launch fits (the host checked the
+// archive's largest command stream), and the stage is read and written with
+// shared-memory instructions.
+template <bool kSmemLut, int kMode, bool kSharedStage>
 __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevArchive &A, const OutView &V,
                                                uint32_t seg, uint32_t epoch, const uint32_t *lut, uint8_t *sstage,
                                                uint32_t scap, uint8_t *gstage, MatchTable *mt, uint16_t *ring,
                                                int lane, uint64_t *ph, uint64_t &ph_t) {
   const SegRec d = A.dir[seg];
   const uint32_t b3 = (4 + A.W) * d.n_cmd;
-  decode_segment_impl<kSmemLut, kMode>(L, A, V, seg, epoch, lut, kSmemLut ? smem_addr(lut) : 0u,
-                                       Stage{b3 <= scap ? sstage : gstage}, mt, smem_addr(ring), lane, d, ph, ph_t);
+  uint8_t *stage = kSharedStage || b3 <= scap ? sstage : gstage;
+  decode_segment_impl<kSmemLut, kMode, kSharedStage>(L, A, V, seg, epoch, lut, kSmemLut ? smem_addr(lut) : 0u,
+                                                     Stage<kSharedStage>{stage, kSharedStage ? smem_addr(stage) : 0u},
+                                                     mt, smem_addr(ring), lane, d, ph, ph_t);
 }
 
 // Dynamic shared memory of a decode CTA: the decode table (64 KiB), then,
@@ -688,12 +723,12 @@ __device__ __forceinline__ WarpSmem warp_smem(uint8_t *smem, int wid) {
 
 #ifdef ACEAPEX_PHASE_CLOCKS
 #define PHASE_DECL        \
-  uint64_t ph[10] = {};   \
+  uint64_t ph[11] = {};   \
   uint64_t ph_t = clock64()
 #define PHASE_FLUSH()                                                                               \
   do {                                                                                              \
     if (lane == 0)                                                                                  \
-      for (int i_ = 0; i_ < 10; ++i_) atomicAdd(&g_phase_cycles[i_], (unsigned long long)ph[i_]); \
+      for (int i_ = 0; i_ < 11; ++i_) atomicAdd(&g_phase_cycles[i_], (unsigned long long)ph[i_]); \
   } while (0)
 #else
 #define PHASE_DECL            \
@@ -707,7 +742,7 @@ __device__ __forceinline__ WarpSmem warp_smem(uint8_t *smem, int wid) {
 // Persistent decode of one archive: its decode table is copied to shared
 // memory once per CTA, and every warp takes the next work item.
 // kMode: how the view maps positions (linear output, ring, or page table).
-template <int kMode>
+template <int kMode, bool kSharedStage>
 __global__ void __launch_bounds__(kDecodeThreads, 1) decode_kernel(DecodeLaunch L) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -729,8 +764,8 @@ __global__ void __launch_bounds__(kDecodeThreads, 1) decode_kernel(DecodeLaunch 
     if (idx >= L.n_work) break;
     if (failed) continue;  // drain the list quickly after an error
     PHASE_MARK(5);
-    decode_segment<true, kMode>(L, L.arc0, L.view0, L.work[idx].seg, epoch, ws.lut, ws.stage, L.stage_cap, gstage,
-                                ws.mt, ws.ring, lane, ph, ph_t);
+    decode_segment<true, kMode, kSharedStage>(L, L.arc0, L.view0, L.work[idx].seg, epoch, ws.lut, ws.stage,
+                                              L.stage_cap, gstage, ws.mt, ws.ring, lane, ph, ph_t);
   }
   PHASE_FLUSH();
 }
@@ -771,8 +806,8 @@ __global__ void __launch_bounds__(kDecodeThreads, 1) batch_kernel(DecodeLaunch L
       if (idx >= A.n_seg) break;
       if (failed) continue;
       PHASE_MARK(5);
-      decode_segment<true, kViewLinear>(L, A, s_V, A.order[idx].seg, epoch, ws.lut, ws.stage, L.stage_cap, gstage,
-                                        ws.mt, ws.ring, lane, ph, ph_t);
+      decode_segment<true, kViewLinear, false>(L, A, s_V, A.order[idx].seg, epoch, ws.lut, ws.stage, L.stage_cap,
+                                               gstage, ws.mt, ws.ring, lane, ph, ph_t);
     }
     __syncthreads();  // the table is replaced only after every warp left this archive
   }
@@ -1172,13 +1207,17 @@ int decode_grid(int device, int block) {
   (void)block;
   int sms = 0, a = 0, b = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  cudaFuncSetAttribute(decode_kernel<kViewLinear>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)kSmemLutBytes);
-  cudaFuncSetAttribute(decode_kernel<kViewRing>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLutBytes);
-  cudaFuncSetAttribute(decode_kernel<kViewPaged>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)kSmemLutBytes);
+  const auto smem = [](const void *k) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLutBytes);
+  };
+  smem((const void *)decode_kernel<kViewLinear, false>);
+  smem((const void *)decode_kernel<kViewRing, false>);
+  smem((const void *)decode_kernel<kViewPaged, false>);
+  smem((const void *)decode_kernel<kViewLinear, true>);
+  smem((const void *)decode_kernel<kViewRing, true>);
+  smem((const void *)decode_kernel<kViewPaged, true>);
   cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLutBytes);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, decode_kernel<kViewLinear>, kDecodeThreads, kSmemLutBytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, decode_kernel<kViewLinear, false>, kDecodeThreads, kSmemLutBytes);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_kernel, kDecodeThreads, kSmemLutBytes);
   int per_sm = a < b ? a : b;
   if (per_sm < 1) per_sm = 1;
@@ -1188,9 +1227,18 @@ int decode_grid(int device, int block) {
 cudaError_t launch_decode(const DecodeLaunch &L, int grid, int block, cudaStream_t st) {
   (void)block;
   if (L.n_work == 0) return cudaSuccess;
-  if (L.view0.page) decode_kernel<kViewPaged><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
-  else if (L.view0.mask != ~uint64_t(0)) decode_kernel<kViewRing><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
-  else decode_kernel<kViewLinear><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
+  // every segment's command streams fit the shared stage: the stage-in-shared kernel
+  const bool sh = L.max_stage <= L.stage_cap;
+  if (L.view0.page) {
+    if (sh) decode_kernel<kViewPaged, true><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
+    else decode_kernel<kViewPaged, false><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
+  } else if (L.view0.mask != ~uint64_t(0)) {
+    if (sh) decode_kernel<kViewRing, true><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
+    else decode_kernel<kViewRing, false><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
+  } else {
+    if (sh) decode_kernel<kViewLinear, true><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
+    else decode_kernel<kViewLinear, false><<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L);
+  }
   return cudaGetLastError();
 }
 
@@ -1465,8 +1513,8 @@ __global__ void __launch_bounds__(256) noalloc_decode_kernel(DecodeLaunch L, uin
       if (lane == 0) latch(L.err, kErrCorrupt);
       continue;
     }
-    decode_segment<false, kViewLinear>(L, A, L.view0, seg, epoch, A.lut, stage, 0, stage, &mts[threadIdx.x >> 5],
-                                       ring, lane, ph, ph_t);
+    decode_segment<false, kViewLinear, false>(L, A, L.view0, seg, epoch, A.lut, stage, 0, stage,
+                                              &mts[threadIdx.x >> 5], ring, lane, ph, ph_t);
   }
 }
 
@@ -1563,15 +1611,16 @@ extern "C" int aceapex_decode_all_noalloc(const void *d_archive, uint64_t nbytes
 // Instrumented build only: copies the warp cycles that the decode kernels
 // spent in each phase (command-class rANS, command parse, literal rANS and
 // placement, dependency waits, match copies, the rest of the work loop) and
-// the event counts (match chunks, copy rounds, copy units, segments) since
-// the last reset into out[0 .. n) (n <= 10), and zeroes them when reset != 0.
+// the event counts (match chunks, copy rounds, copy units, segments, chunks
+// that waited) since the last reset into out[0 .. n) (n <= 11), and zeroes
+// them when reset != 0.
 // Synchronises the current device. Returns 0, or 4 on a CUDA error.
 extern "C" int aceapex_phase_cycles(uint64_t *out, int n, int reset) {
   unsigned long long h[16] = {};
   if (cudaDeviceSynchronize() != cudaSuccess ||
       cudaMemcpyFromSymbol(h, aceapex::g_phase_cycles, sizeof(h)) != cudaSuccess)
     return 4;
-  for (int i = 0; i < n && i < 10; ++i) out[i] = h[i];
+  for (int i = 0; i < n && i < 11; ++i) out[i] = h[i];
   if (reset) {
     const unsigned long long z[16] = {};
     if (cudaMemcpyToSymbol(aceapex::g_phase_cycles, z, sizeof(z)) != cudaSuccess) return 4;

@@ -57,6 +57,7 @@ struct DecodeLaunch {
   uint32_t scratch_warps;   // number of per-warp staging slots
   uint32_t active_warps;    // warps per CTA that take work (<= kDecodeThreads / 32)
   uint32_t stage_cap;       // bytes of a warp's shared staging to use (<= kSmemStage)
+  uint32_t max_stage;       // largest command stream (bytes) of any segment the launch may decode
 };
 
 constexpr uint32_t kStageBytes = kMaxSym;  // global staging slot: all decoded symbols of one segment
