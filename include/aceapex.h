@@ -218,8 +218,11 @@ int aceapex_decode_batch(aceapex_archive *const *as, int n, void *const *d_outs,
  *
  * aceapex_server_submit: queue bytes [byte_lo, byte_hi) of archive `arc`, to
  * be written to the device buffer d_dst (cap bytes, caller-owned, must stay
- * valid until the request completes). Returns a ticket. EBUSY: the request's
- * closure alone exceeds a slot's arena (admission refused); ERANGE, EINVAL.
+ * valid until the request completes). Returns a ticket; the request's
+ * transitive source closure is walked afterwards by the server's walker
+ * threads, so the call itself only enqueues. EBUSY: the range's own segments
+ * exceed a slot's arena (admission refused at once); a wider closure that can
+ * never fit completes the request with status EBUSY instead. ERANGE, EINVAL.
  *
  * aceapex_server_poll: *done = 1 once the request completed (then the ticket
  * is released, the return value is the request's status and *latency_ms the

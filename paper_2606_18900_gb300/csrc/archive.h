@@ -125,7 +125,7 @@ struct aceapex_archive {
   int max_grid = 0;   // occupancy limit (scratch is sized for it)
   uint32_t active_warps = kDecodeThreads / 32;
   uint32_t stage_cap = kSmemStage;
-  uint32_t max_cmd_syms = 0;  // largest n_cmd * (4 + W) of any segment
+  uint32_t max_cmd_syms = 0;  // largest command stage of any segment: n_cmd * (4 + W) + 4 bytes
   uint64_t wait_ns = kDefaultWaitNs;
   bool any_blocked = false;
 
@@ -216,6 +216,9 @@ OutView linear_view(uint8_t *base, uint64_t origin);
 // with max_edges > 0, gives up (returns false) after visiting that many
 // dependency entries
 bool closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, std::vector<uint32_t> &out, uint64_t max_edges = 0);
+// the same walk with caller-owned marks (one set per thread that walks)
+bool closure_with(const aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, std::vector<uint32_t> &mark, uint32_t &gen,
+                  std::vector<uint32_t> &out, uint64_t max_edges = 0);
 // the same for a list of seed segments; marks with a fresh generation of A->mark
 void closure_of(aceapex_archive *A, const uint32_t *seeds, uint64_t n, std::vector<uint32_t> &out);
 

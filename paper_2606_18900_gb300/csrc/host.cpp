@@ -126,7 +126,7 @@ int validate(const uint8_t *a, uint64_t len, aceapex_archive *A) {
     const uint64_t out_size = std::min<uint64_t>(S, h.n - s * S);
     if (r.n_lit > out_size || (uint64_t)r.n_cmd * h.min_match > out_size - r.n_lit) return ACEAPEX_ECORRUPT;
     po = round16(po + 128 + 2 * (uint64_t)r.n_words);
-    A->max_cmd_syms = std::max<uint32_t>(A->max_cmd_syms, r.n_cmd * (4 + h.W));
+    A->max_cmd_syms = std::max<uint32_t>(A->max_cmd_syms, r.n_cmd * (4 + h.W) + 4);
     n_lit += r.n_lit;
     n_cmd += r.n_cmd;
     max_lv = std::max<uint32_t>(max_lv, r.level);
@@ -270,18 +270,19 @@ OutView linear_view(uint8_t *base, uint64_t origin) {
 }
 
 // transitive source closure of segments [s_lo, s_hi] (host, from the stored lists)
-bool closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, std::vector<uint32_t> &out, uint64_t max_edges) {
-  if (A->mark.size() != A->h.n_seg) A->mark.assign(A->h.n_seg, 0);
-  if (++A->mark_gen == 0) {
-    std::fill(A->mark.begin(), A->mark.end(), 0);
-    A->mark_gen = 1;
+bool closure_with(const aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, std::vector<uint32_t> &mark, uint32_t &gen,
+                  std::vector<uint32_t> &out, uint64_t max_edges) {
+  if (mark.size() != A->h.n_seg) mark.assign(A->h.n_seg, 0);
+  if (++gen == 0) {
+    std::fill(mark.begin(), mark.end(), 0);
+    gen = 1;
   }
-  const uint32_t g = A->mark_gen;
+  const uint32_t g = gen;
   out.clear();
   std::vector<uint32_t> stack;
   for (uint64_t s = s_lo; s <= s_hi; ++s)
-    if (A->mark[s] != g) {
-      A->mark[s] = g;
+    if (mark[s] != g) {
+      mark[s] = g;
       stack.push_back((uint32_t)s);
     }
   uint64_t edges = 0;
@@ -293,13 +294,17 @@ bool closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, std::vector<uint3
     if (max_edges && edges > max_edges) return false;
     for (uint64_t i = A->dep_ptr[s]; i < A->dep_ptr[s + 1]; ++i) {
       uint32_t d = A->deps[i];
-      if (A->mark[d] != g) {
-        A->mark[d] = g;
+      if (mark[d] != g) {
+        mark[d] = g;
         stack.push_back(d);
       }
     }
   }
   return true;
+}
+
+bool closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, std::vector<uint32_t> &out, uint64_t max_edges) {
+  return closure_with(A, s_lo, s_hi, A->mark, A->mark_gen, out, max_edges);
 }
 
 void closure_of(aceapex_archive *A, const uint32_t *seeds, uint64_t n, std::vector<uint32_t> &out) {

@@ -216,6 +216,10 @@ struct Stage {
     if (kShared) asm volatile("st.shared.u16 [%0], %1;" ::"r"(s + o), "h"((uint16_t)v) : "memory");
     else *reinterpret_cast<uint16_t *>(p + o) = (uint16_t)v;
   }
+  __device__ __forceinline__ void st32(uint32_t o, uint32_t v) const {
+    if (kShared) asm volatile("st.shared.u32 [%0], %1;" ::"r"(s + o), "r"(v) : "memory");
+    else *reinterpret_cast<uint32_t *>(p + o) = v;
+  }
   // W-byte little-endian value at offset o (1 <= W <= 8); reads only the
   // aligned 4-byte words that hold bytes of [o, o + W), so never past the
   // word that holds byte o + W - 1
@@ -364,6 +368,18 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
     return sym;
   };
 
+  // Stage layout: command c's literal-run length (after the parse: the run's
+  // end in literal numbering) and match length less min_match as one 32-bit
+  // record (u16, u16) at 4 c; at 4 nc a sentinel record whose run end (65535)
+  // lies beyond every literal; the W-byte offsets from 4 nc + 4. Symbol q of
+  // the command classes goes to stage_off(q).
+  auto stage_off = [&](uint32_t q) -> uint32_t {
+    if (q < b1) return 4 * (q >> 1) + (q & 1);
+    if (q < b2) return 4 * ((q - b1) >> 1) + 2 + ((q - b1) & 1);
+    return q + 4;
+  };
+  const uint32_t offs = b2 + 4;  // the offsets' start
+
   // (1) command classes; the step that crosses into the literals keeps its
   // literal symbol in `pend` until the command prefixes exist. Four steps take
   // at most 128 words, so after an advance() (blocks blk and blk + 1 complete,
@@ -381,18 +397,22 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
       const uint32_t c_lo = (uint32_t)(t0 >= b1) + (uint32_t)(t0 >= b2);
       const uint32_t c_hi = (uint32_t)(t0 + 127 >= b1) + (uint32_t)(t0 + 127 >= b2);
       if (c_lo == c_hi) {
+        const uint32_t base = c_lo == 0 ? 0u : c_lo == 1 ? b1 : b2;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) st.st8(t0 + 32 * u + lane, cls_step(c_lo << kScaleBits));
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t k = t0 + 32 * u + lane - base;  // symbol number within the class
+          st.st8(c_lo == 2 ? b2 + 4 + k : 4 * (k >> 1) + 2 * c_lo + (k & 1), cls_step(c_lo << kScaleBits));
+        }
       } else {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) st.st8(t0 + 32 * u + lane, cmd_step(t0 + 32 * u + lane));
+        for (int u = 0; u < 4; ++u) st.st8(stage_off(t0 + 32 * u + lane), cmd_step(t0 + 32 * u + lane));
       }
       advance();
     }
     for (; t0 < b3; t0 += 32) {
       const uint32_t q = t0 + lane;
       const uint32_t sym = cmd_step(q);
-      if (q < b3) st.st8(q, sym);
+      if (q < b3) st.st8(stage_off(q), sym);
       else pend = sym;
       advance();
     }
@@ -408,9 +428,10 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
     uint32_t ll = 0, ml = 0;
     uint64_t src = 0;
     if (valid) {
-      ll = st.u16(2 * c);
-      ml = st.u16(b1 + 2 * c) + mm;
-      src = st.le(b2 + W * c, W);
+      const uint32_t rec = st.u32(4 * c);
+      ll = rec & 0xFFFFu;
+      ml = (rec >> 16) + mm;
+      src = st.le(offs + W * c, W);
     }
     const uint32_t inc_l = warp_incl_scan(ll, lane), inc_m = warp_incl_scan(ml, lane);
     const uint32_t lit_end = tot_l + inc_l, msum = tot_m + inc_m - ml;
@@ -422,11 +443,12 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
       ok = false;
       break;
     }
-    if (valid) st.st16(2 * c, lit_end);
+    if (valid) st.st16(4 * c, lit_end);
     tot_l += __shfl_sync(kFull, inc_l, 31);
     tot_m += __shfl_sync(kFull, inc_m, 31);
   }
   if (ok && (tot_l + tot_m > out_size || out_size - tot_m != nl)) ok = false;
+  if (ok && lane == 0) st.st32(4 * nc, 0xFFFFu);
   __syncwarp();
   PHASE_MARK(1);
 
@@ -434,10 +456,9 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
   // the literal run of command cu (literal number), the next boundary; p: the
   // lane's output address for its literal of the current step.
   if (ok) {
-    constexpr int kInf = 0x3FFFFFFF;
     int K0 = (b3 & 31u) ? (int)(b3 & ~31u) - (int)b3 : 0;
-    uint32_t cu = 0;
-    int E = nc ? (int)st.u16(0) : kInf;
+    uint32_t cu = 0, rec = st.u32(0);
+    int E = (int)(rec & 0xFFFFu);
     uint8_t *p = out + K0 + lane;
     // Commands whose runs end inside [K0, K0 + 32): the lanes at or after a
     // run's end skip that command's match bytes in this step already, the
@@ -445,11 +466,11 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
     auto bound = [&](uint32_t &dq) -> bool {
       if (E - K0 >= 32) return false;
       do {
-        const uint32_t ml = st.u16(b1 + 2 * cu) + mm;
+        const uint32_t ml = (rec >> 16) + mm;
         if (lane >= E - K0) p += ml;
         else dq += ml;
-        ++cu;
-        E = cu < nc ? (int)st.u16(2 * cu) : kInf;
+        rec = st.u32(4 * ++cu);
+        E = (int)(rec & 0xFFFFu);
       } while (E - K0 < 32);
       return true;
     };
@@ -522,9 +543,10 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
     uint32_t ml = 0, lend = 0;
     uint64_t src = 0;
     if (valid) {
-      ml = st.u16(b1 + 2 * c) + mm;
-      lend = st.u16(2 * c);
-      src = st.le(b2 + W * c, W);
+      const uint32_t rec = st.u32(4 * c);
+      ml = (rec >> 16) + mm;
+      lend = rec & 0xFFFFu;
+      src = st.le(offs + W * c, W);
     }
     const uint32_t inc_m = warp_incl_scan(ml, lane);
     const uint64_t dst = valid ? seg_start + lend + (mbase + inc_m - ml) : ~uint64_t(0);
@@ -694,7 +716,7 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
                                                int lane, uint64_t *ph, uint64_t &ph_t) {
   const SegRec d = A.dir[seg];
   const uint32_t b3 = (4 + A.W) * d.n_cmd;
-  uint8_t *stage = kSharedStage || b3 <= scap ? sstage : gstage;
+  uint8_t *stage = kSharedStage || b3 + 4 <= scap ? sstage : gstage;
   decode_segment_impl<kSmemLut, kMode, kSharedStage>(L, A, V, seg, epoch, lut, kSmemLut ? smem_addr(lut) : 0u,
                                                      Stage<kSharedStage>{stage, kSharedStage ? smem_addr(stage) : 0u},
                                                      mt, smem_addr(ring), lane, d, ph, ph_t);

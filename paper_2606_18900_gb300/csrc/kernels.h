@@ -57,10 +57,12 @@ struct DecodeLaunch {
   uint32_t scratch_warps;   // number of per-warp staging slots
   uint32_t active_warps;    // warps per CTA that take work (<= kDecodeThreads / 32)
   uint32_t stage_cap;       // bytes of a warp's shared staging to use (<= kSmemStage)
-  uint32_t max_stage;       // largest command stream (bytes) of any segment the launch may decode
+  uint32_t max_stage;       // largest command stage (bytes) of any segment the launch may decode
 };
 
-constexpr uint32_t kStageBytes = kMaxSym;  // global staging slot: all decoded symbols of one segment
+// command stage of a segment: its n_cmd * (4 + W) command symbols plus a
+// 4-byte sentinel record; the global slot holds the largest possible one
+constexpr uint32_t kStageBytes = kMaxSym + 16;
 constexpr uint32_t kDecodeThreads = 1024;  // decode CTA: 32 warps, one CTA per SM
 constexpr uint32_t kSmemStage = 3072;      // per-warp shared staging for the command streams
 constexpr uint32_t kLutBytes = 4 * kScale * 4;

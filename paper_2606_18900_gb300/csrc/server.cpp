@@ -2,8 +2,10 @@
 // device-resident archives (the serving pattern of the method's random access,
 // paper §4 and §4.1, applied to many concurrent requests).
 //
-// One worker thread owns the GPU side. Requests enter a FIFO queue; their
-// transitive source closures are computed when they are submitted. Whenever
+// One worker thread owns the GPU side. A submitted request goes to a pool of
+// walker threads, which compute its transitive source closure (each with its
+// own marks) and then append it to a FIFO queue; a submission itself only
+// enqueues, so callers can offer requests at their own rate. Whenever
 // one of `slots` batch slots is free, the worker takes requests from the head
 // of the queue while the union of their closures fits the slot's decode arena
 // (the device-memory budget is split evenly over the slots), then on the
@@ -68,12 +70,14 @@ struct aceapex_server {
   std::vector<std::vector<uint32_t>> mark;  // per archive, for batch unions
   uint32_t mark_gen = 0;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
-  std::deque<uint64_t> queue;
+  std::condition_variable cv_work, cv_done, cv_pending;
+  std::deque<uint64_t> pending;  // submitted, closure not yet walked
+  std::deque<uint64_t> queue;    // closure known, waiting for admission
   std::unordered_map<uint64_t, Req> reqs;
   uint64_t next_id = 1;
   bool stop = false;
   std::thread worker;
+  std::vector<std::thread> walkers;
   aceapex_server_stats st{};
   uint32_t inflight = 0;
 };
@@ -169,6 +173,37 @@ int launch_batch_on(aceapex_server *S, Slot &slot, const std::vector<Req *> &bat
   return e == cudaSuccess ? ACEAPEX_OK : ACEAPEX_ECUDA;
 }
 
+// Closure walker: takes submitted requests, walks their closures outside the
+// lock with its own marks (one set per archive), and queues them for
+// admission, or completes them with EBUSY when the closure can never fit a
+// slot's arena.
+void walker_loop(aceapex_server *S) {
+  std::vector<std::vector<uint32_t>> mark(S->arcs.size());
+  std::vector<uint32_t> gen(S->arcs.size(), 0);
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    S->cv_pending.wait(lk, [&] { return S->stop || !S->pending.empty(); });
+    if (S->pending.empty()) break;  // stopping
+    const uint64_t id = S->pending.front();
+    S->pending.pop_front();
+    Req *r = &S->reqs[id];
+    lk.unlock();
+    aceapex_archive *A = S->arcs[r->arc];
+    closure_with(A, r->lo >> A->h.log2_S, (r->hi - 1) >> A->h.log2_S, mark[r->arc], gen[r->arc], r->segs);
+    lk.lock();
+    if (r->segs.size() > S->cap_segs) {
+      r->status = ACEAPEX_EBUSY;
+      r->latency_ms = now_ms() - r->t_submit;
+      r->done = true;
+      S->st.refused++;
+      S->cv_done.notify_all();
+    } else {
+      S->queue.push_back(id);
+      S->cv_work.notify_one();
+    }
+  }
+}
+
 void worker_loop(aceapex_server *S) {
   cudaSetDevice(S->device);
   std::unique_lock<std::mutex> lk(S->mu);
@@ -236,7 +271,7 @@ void worker_loop(aceapex_server *S) {
       }
       progressed = true;
     }
-    if (S->stop && S->queue.empty() && S->inflight == 0) break;
+    if (S->stop && S->queue.empty() && S->pending.empty() && S->inflight == 0) break;
     if (!progressed) {
       if (S->inflight) S->cv_work.wait_for(lk, std::chrono::microseconds(20));
       else S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
@@ -304,6 +339,9 @@ int aceapex_server_create(aceapex_archive *const *as, int n, uint64_t mem_budget
     }
   }
   S->worker = std::thread(worker_loop, S);
+  const unsigned hw = std::thread::hardware_concurrency();
+  const unsigned nw = std::max(1u, std::min(8u, hw / 2));
+  for (unsigned i = 0; i < nw; ++i) S->walkers.emplace_back(walker_loop, S);
   *out = S;
   return ACEAPEX_OK;
 }
@@ -315,6 +353,9 @@ void aceapex_server_destroy(aceapex_server *S) {
     S->stop = true;
   }
   S->cv_work.notify_all();
+  S->cv_pending.notify_all();
+  for (std::thread &t : S->walkers)
+    if (t.joinable()) t.join();
   if (S->worker.joinable()) S->worker.join();
   cudaSetDevice(S->device);
   for (Slot &slot : S->slots) {
@@ -344,19 +385,21 @@ int aceapex_server_submit(aceapex_server *S, int arc, uint64_t lo, uint64_t hi, 
   r.lo = lo;
   r.hi = hi;
   r.dst = static_cast<uint8_t *>(d_dst);
+  r.t_submit = now_ms();  // the latency includes the closure walk
   std::unique_lock<std::mutex> lk(S->mu);
   S->st.submitted++;
-  closure(A, lo >> A->h.log2_S, (hi - 1) >> A->h.log2_S, r.segs);
-  if (r.segs.size() > S->cap_segs) {  // could never be admitted under the budget
+  // a closure holds at least the range's own segments: a range that alone
+  // exceeds a slot's arena can never be admitted (wider closures are found
+  // by the walker, which completes the request with EBUSY)
+  if (((hi - 1) >> A->h.log2_S) - (lo >> A->h.log2_S) + 1 > S->cap_segs) {
     S->st.refused++;
     return ACEAPEX_EBUSY;
   }
-  r.t_submit = now_ms();
   const uint64_t id = S->next_id++;
   S->reqs.emplace(id, std::move(r));
-  S->queue.push_back(id);
+  S->pending.push_back(id);
   lk.unlock();
-  S->cv_work.notify_one();
+  S->cv_pending.notify_one();
   *ticket = id;
   return ACEAPEX_OK;
 }
@@ -399,7 +442,7 @@ int aceapex_server_get_stats(aceapex_server *S, aceapex_server_stats *out) {
   if (!S || !out) return ACEAPEX_EINVAL;
   std::lock_guard<std::mutex> lk(S->mu);
   *out = S->st;
-  out->queued = S->queue.size();
+  out->queued = S->queue.size() + S->pending.size();
   out->slot_segments = S->cap_segs;
   return ACEAPEX_OK;
 }

@@ -13,7 +13,7 @@ import oracle
 import paper_2606_18900_gb300 as ace
 import synth
 
-INF = 0x3FFFFFFF
+INF = 0xFFFF  # the sentinel record after the last command: beyond every literal
 
 
 def cursor_positions(ll, ml, n_sym, b3):
