@@ -277,7 +277,7 @@ def random_reads(arc, data, n, seed, stream, device):
     return lat, ok, closure
 
 
-PHASES = ("cmd_rans", "parse", "lit_rans", "waits", "copies", "loop")
+PHASES = ("cmd_rans", "parse", "lit_rans", "src_checks", "copies", "loop", "dep_waits")
 COUNTS = ("chunks", "rounds", "units", "segments", "waited_chunks")
 
 
@@ -295,22 +295,22 @@ def phase_child(args):
     L = ace.lib()
     L.aceapex_phase_cycles.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
     L.aceapex_phase_cycles.restype = ctypes.c_int
-    buf = (ctypes.c_uint64 * 11)()
+    buf = (ctypes.c_uint64 * 12)()
     with ace.Archive(arc_bytes) as a:
         out = torch.empty(a.size, dtype=torch.uint8, device="cuda")
         stream = torch.cuda.Stream()
         for _ in range(2):
             a.decode_all(out, stream)
         a.check(stream)
-        if L.aceapex_phase_cycles(buf, 11, 1):
+        if L.aceapex_phase_cycles(buf, 12, 1):
             raise SystemExit("phase counters unavailable")
         reps = 5
         for _ in range(reps):
             a.decode_all(out, stream)
         a.check(stream)
-        if L.aceapex_phase_cycles(buf, 11, 1):
+        if L.aceapex_phase_cycles(buf, 12, 1):
             raise SystemExit("phase counters unavailable")
-    cyc = [int(v) for v in buf[:6]]
+    cyc = [int(v) for v in buf[:6]] + [int(buf[11])]
     tot = sum(cyc)
     print(json.dumps({"share": {k: v / tot for k, v in zip(PHASES, cyc)},
                       "per_decode": {k: int(v) // reps for k, v in zip(COUNTS, buf[6:11])}}), flush=True)
@@ -335,7 +335,7 @@ def phase_split(arc_bytes, ms_decode, U):
     j = json.loads(r.stdout.strip().splitlines()[-1])
     sh = j["share"]
     ent = sh["cmd_rans"] + sh["parse"] + sh["lit_rans"]
-    mat = sh["waits"] + sh["copies"]
+    mat = sh["src_checks"] + sh["copies"] + sh["dep_waits"]
     return {"what": "share of the decode kernel's warp cycles per phase (clock64 counters in a separate build), "
                     "applied to the plain build's median kernel time",
             "entropy_ms": ent * ms_decode, "match_ms": mat * ms_decode, "other_ms": sh["loop"] * ms_decode,

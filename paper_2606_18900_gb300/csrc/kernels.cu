@@ -238,10 +238,12 @@ struct Stage {
 
 #ifdef ACEAPEX_PHASE_CLOCKS
 // Warp-cycle counters per phase (instrumented build only): 0 command-class
-// rANS, 1 command parse, 2 literal rANS and placement, 3 dependency waits,
+// rANS, 1 command parse, 2 literal rANS and placement, 3 source checks of
+// the match chunks,
 // 4 match copies, 5 the rest of the work loop; then event counts: 6 match
 // chunks, 7 copy rounds, 8 copy units, 9 segments, 10 chunks whose source
-// flags were not all set at the first reading.
+// flags were not all set at the first reading; 11 warp cycles spent waiting
+// for those flags (counted apart from phase 3, the chunks' source checks).
 __device__ unsigned long long g_phase_cycles[16];
 #define PHASE_COUNT(i, v) \
   do {                    \
@@ -552,6 +554,13 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
     const uint64_t dst = valid ? seg_start + lend + (mbase + inc_m - ml) : ~uint64_t(0);
     mbase += __shfl_sync(kFull, inc_m, 31);
     const uint64_t q0 = src >> log2_S, q1 = valid ? (src + ml - 1) >> log2_S : q0;
+    // start moving the chunk's source bytes (the first and the last 128-byte
+    // line of each match's) toward L2 while the checks and hazards run
+    if (kMode != kViewPaged && valid) {
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(src_at<kMode>(V, src, log2_S)));
+      if (((src ^ (src + ml - 1)) >> 7) != 0)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(src_at<kMode>(V, src + ml - 1, log2_S)));
+    }
     const bool need0 = valid && q0 != seg;
     const bool need1 = valid && q1 != q0 && q1 != seg;
     // A source segment must have a lower level than ours (a wait on any other
@@ -575,11 +584,13 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
     }
     if (!__all_sync(kFull, f0 == epoch && f1 == epoch)) {
       PHASE_COUNT(10, 1);
+      PHASE_MARK(3);
       if (!wait_flags(A.flags + (need0 ? q0 : 0), need0, epoch, deadline, L.err, lane) ||
           !wait_flags(A.flags + (need1 ? q1 : 0), need1, epoch, deadline, L.err, lane)) {
         ok = false;
         break;
       }
+      PHASE_MARK(11);
     }
     PHASE_MARK(3);
     PHASE_COUNT(6, 1);
@@ -745,12 +756,12 @@ __device__ __forceinline__ WarpSmem warp_smem(uint8_t *smem, int wid) {
 
 #ifdef ACEAPEX_PHASE_CLOCKS
 #define PHASE_DECL        \
-  uint64_t ph[11] = {};   \
+  uint64_t ph[12] = {};   \
   uint64_t ph_t = clock64()
 #define PHASE_FLUSH()                                                                               \
   do {                                                                                              \
     if (lane == 0)                                                                                  \
-      for (int i_ = 0; i_ < 11; ++i_) atomicAdd(&g_phase_cycles[i_], (unsigned long long)ph[i_]); \
+      for (int i_ = 0; i_ < 12; ++i_) atomicAdd(&g_phase_cycles[i_], (unsigned long long)ph[i_]); \
   } while (0)
 #else
 #define PHASE_DECL            \
@@ -1632,17 +1643,18 @@ extern "C" int aceapex_decode_all_noalloc(const void *d_archive, uint64_t nbytes
 #ifdef ACEAPEX_PHASE_CLOCKS
 // Instrumented build only: copies the warp cycles that the decode kernels
 // spent in each phase (command-class rANS, command parse, literal rANS and
-// placement, dependency waits, match copies, the rest of the work loop) and
-// the event counts (match chunks, copy rounds, copy units, segments, chunks
-// that waited) since the last reset into out[0 .. n) (n <= 11), and zeroes
-// them when reset != 0.
+// placement, source checks, match copies, the rest of the work loop), the
+// event counts (match chunks, copy rounds, copy units, segments, chunks that
+// waited) and the cycles spent waiting for source segments, in that order,
+// since the last reset into out[0 .. n) (n <= 12), and zeroes them when
+// reset != 0.
 // Synchronises the current device. Returns 0, or 4 on a CUDA error.
 extern "C" int aceapex_phase_cycles(uint64_t *out, int n, int reset) {
   unsigned long long h[16] = {};
   if (cudaDeviceSynchronize() != cudaSuccess ||
       cudaMemcpyFromSymbol(h, aceapex::g_phase_cycles, sizeof(h)) != cudaSuccess)
     return 4;
-  for (int i = 0; i < n && i < 11; ++i) out[i] = h[i];
+  for (int i = 0; i < n && i < 12; ++i) out[i] = h[i];
   if (reset) {
     const unsigned long long z[16] = {};
     if (cudaMemcpyToSymbol(aceapex::g_phase_cycles, z, sizeof(z)) != cudaSuccess) return 4;
