@@ -370,11 +370,13 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
     return sym;
   };
 
-  // Stage layout: command c's literal-run length (after the parse: the run's
-  // end in literal numbering) and match length less min_match as one 32-bit
-  // record (u16, u16) at 4 c; at 4 nc a sentinel record whose run end (65535)
-  // lies beyond every literal; the W-byte offsets from 4 nc + 4. Symbol q of
-  // the command classes goes to stage_off(q).
+  // Stage layout: command c's literal-run length and match length less
+  // min_match as one 32-bit record (u16, u16) at 4 c, which the parse
+  // replaces by the run's end in literal numbering and the match bytes of
+  // commands 0..c (both below 2^16: a segment holds at most 16 KiB); at 4 nc
+  // a sentinel record whose run end (65535) lies beyond every literal; the
+  // W-byte offsets from 4 nc + 4. Symbol q of the command classes goes to
+  // stage_off(q).
   auto stage_off = [&](uint32_t q) -> uint32_t {
     if (q < b1) return 4 * (q >> 1) + (q & 1);
     if (q < b2) return 4 * ((q - b1) >> 1) + 2 + ((q - b1) & 1);
@@ -445,7 +447,7 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
       ok = false;
       break;
     }
-    if (valid) st.st16(4 * c, lit_end);
+    if (valid) st.st32(4 * c, lit_end | (msum + ml) << 16);
     tot_l += __shfl_sync(kFull, inc_l, 31);
     tot_m += __shfl_sync(kFull, inc_m, 31);
   }
@@ -455,26 +457,26 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
   PHASE_MARK(1);
 
   // (3) literals. K0: literal number of lane 0 in the current step; E: end of
-  // the literal run of command cu (literal number), the next boundary; p: the
-  // lane's output address for its literal of the current step.
+  // the literal run of command cu (literal number), the next boundary; Sc:
+  // match bytes before the literals from the current boundary on (the
+  // cumulative match length through command cu - 1); outK: the output
+  // address of literal K0 before any match byte.
   if (ok) {
     int K0 = (b3 & 31u) ? (int)(b3 & ~31u) - (int)b3 : 0;
-    uint32_t cu = 0, rec = st.u32(0);
+    uint32_t cu = 0, rec = st.u32(0), Sc = 0;
     int E = (int)(rec & 0xFFFFu);
-    uint8_t *p = out + K0 + lane;
-    // Commands whose runs end inside [K0, K0 + 32): the lanes at or after a
-    // run's end skip that command's match bytes in this step already, the
-    // lanes before it from the next step on (dq, added after the store).
-    auto bound = [&](uint32_t &dq) -> bool {
-      if (E - K0 >= 32) return false;
-      do {
-        const uint32_t ml = (rec >> 16) + mm;
-        if (lane >= E - K0) p += ml;
-        else dq += ml;
+    uint8_t *outK = out + K0;
+    // The lane's offset for this step: lanes at or after a run end that lies
+    // inside [K0, K0 + 32) take that command's cumulative match length.
+    auto bound = [&]() -> uint32_t {
+      uint32_t sl = Sc;
+      while (E - K0 < 32) {
+        Sc = rec >> 16;
+        if (lane >= E - K0) sl = Sc;
         rec = st.u32(4 * ++cu);
         E = (int)(rec & 0xFFFFu);
-      } while (E - K0 < 32);
-      return true;
+      }
+      return sl + (uint32_t)lane;
     };
     auto lit_rans = [&]() -> uint32_t {
       const uint32_t e = entry((3u << kScaleBits) | (x & (kScale - 1)));
@@ -483,51 +485,46 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
       return e;
     };
     if (b3 & 31u) {  // the crossing step, decoded in (1)
-      uint32_t dq = 0;
-      const bool hb = bound(dq);
-      if (lane >= -K0 && t0 - 32 + lane < n_sym) *p = (uint8_t)pend;
-      if (hb) p += dq;
-      p += 32;
+      const uint32_t o = bound();
+      if (lane >= -K0 && t0 - 32 + lane < n_sym) outK[o] = (uint8_t)pend;
+      outK += 32;
       K0 += 32;
     }
     for (; t0 + 128 <= n_sym; t0 += 128) {
       if (E - K0 >= 128) {  // no run ends inside these four steps
+        uint8_t *p = outK + (Sc + (uint32_t)lane);
 #pragma unroll
         for (int u = 0; u < 4; ++u) p[32 * u] = (uint8_t)lit_rans();
-        K0 += 128;
       } else {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          uint32_t dq = 0;
-          const bool hb = bound(dq);
-          p[32 * u] = (uint8_t)lit_rans();
-          if (hb) p += dq;
+          const uint32_t o = bound();
+          outK[32 * u + o] = (uint8_t)lit_rans();
           K0 += 32;
         }
+        K0 -= 128;
       }
-      p += 128;
+      K0 += 128;
+      outK += 128;
       advance();
     }
     for (; t0 + 32 <= n_sym; t0 += 32) {
-      uint32_t dq = 0;
-      const bool hb = bound(dq);
-      *p = (uint8_t)lit_rans();
-      if (hb) p += dq;
-      p += 32;
+      const uint32_t o = bound();
+      outK[o] = (uint8_t)lit_rans();
+      outK += 32;
       K0 += 32;
       advance();
     }
     if (t0 < n_sym) {
       const bool active = t0 + lane < n_sym;
-      uint32_t dq = 0;
-      bound(dq);
+      const uint32_t o = bound();
       uint32_t e = 0;
       if (active) {
         e = entry((3u << kScaleBits) | (x & (kScale - 1)));
         x = ((e >> 20) + 1u) * (x >> kScaleBits) + ((e >> 8) & 0xFFFu);
       }
       renorm(active && x < kRansL);
-      if (active) *p = (uint8_t)e;
+      if (active) outK[o] = (uint8_t)e;
       t0 += 32;
     }
   }
@@ -538,21 +535,25 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
   // (4) matches
   const uint32_t my_level = d.level;
   const uint64_t deadline = now_ns() + L.wait_ns;
-  uint32_t mbase = 0;
+  uint32_t mbase = 0;  // match bytes before the chunk
   for (uint32_t c0 = 0; ok && c0 < nc; c0 += 32) {
     const uint32_t c = c0 + lane;
     const bool valid = c < nc;
-    uint32_t ml = 0, lend = 0;
+    uint32_t ml = 0, lend = 0, cum = 0;
     uint64_t src = 0;
     if (valid) {
       const uint32_t rec = st.u32(4 * c);
-      ml = (rec >> 16) + mm;
+      cum = rec >> 16;
       lend = rec & 0xFFFFu;
       src = st.le(offs + W * c, W);
     }
-    const uint32_t inc_m = warp_incl_scan(ml, lane);
-    const uint64_t dst = valid ? seg_start + lend + (mbase + inc_m - ml) : ~uint64_t(0);
-    mbase += __shfl_sync(kFull, inc_m, 31);
+    // match bytes of the commands before c (the previous lane's sum, or the
+    // last sum of the previous chunk); this command's length is the difference
+    const uint32_t up = __shfl_up_sync(kFull, cum, 1);
+    const uint32_t before = lane ? up : mbase;
+    if (valid) ml = cum - before;
+    const uint64_t dst = valid ? seg_start + lend + before : ~uint64_t(0);
+    mbase = __shfl_sync(kFull, cum, min(nc - 1 - c0, 31u));
     const uint64_t q0 = src >> log2_S, q1 = valid ? (src + ml - 1) >> log2_S : q0;
     // start moving the chunk's source bytes (the first and the last 128-byte
     // line of each match's) toward L2 while the checks and hazards run
