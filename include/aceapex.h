@@ -71,8 +71,16 @@ typedef struct {
 int aceapex_open(const void *h_archive, uint64_t nbytes, int device, aceapex_archive **out);
 
 /* Release every device and host resource of the handle (NULL is a no-op).
- * Synchronises the device first so that no kernel still uses them. */
+ * Synchronises the device first so that no kernel still uses them. Device
+ * memory goes back to the library's per-device pool, which keeps up to
+ * 8 GiB of freed memory for later opens (an open after a close then
+ * allocates nothing from the driver); aceapex_release_cached_memory returns
+ * it to the driver. */
 void aceapex_close(aceapex_archive *a);
+
+/* Return the device memory that the library's pool on `device` keeps for
+ * reuse (memory of open handles stays allocated). Errors: ECUDA. */
+int aceapex_release_cached_memory(int device);
 
 /* Decompressed size N of the archive (0 for NULL). */
 uint64_t aceapex_decoded_size(const aceapex_archive *a);

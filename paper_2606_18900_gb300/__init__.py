@@ -131,6 +131,7 @@ def lib():
             L.aceapex_open.argtypes = [vp, u64, i32, ctypes.POINTER(vp)]
             L.aceapex_close.argtypes = [vp]
             L.aceapex_close.restype = None
+            L.aceapex_release_cached_memory.argtypes = [i32]
             L.aceapex_decoded_size.argtypes = [vp]
             L.aceapex_decoded_size.restype = u64
             L.aceapex_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
@@ -312,6 +313,12 @@ def fastq_index(data) -> np.ndarray:
     out = np.zeros(max(n, 1), dtype=np.uint64)
     L.aceapex_fastq_index(buf.ctypes.data, buf.size, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), n)
     return out[:n]
+
+
+def release_cached_memory(device: int = 0):
+    """Return the device memory that the library keeps for reuse after
+    closes on `device` (aceapex_release_cached_memory)."""
+    _check(lib().aceapex_release_cached_memory(int(device)), "aceapex_release_cached_memory")
 
 
 def fastq_split(data):

@@ -29,19 +29,32 @@ T rd(const uint8_t *p) {
 // on a device, so a ready flag can never be mistaken for one of another call.
 uint32_t *global_epoch(int device);
 
+// Device memory of the library's buffers (host.cpp): allocations on the
+// current device come from a per-device pool that keeps up to
+// kPoolKeepBytes of freed memory for later allocations, so an archive opened
+// after another was closed reuses its memory instead of asking the driver;
+// dev_free first waits for the whole device, as cudaFree does, since any
+// stream may still use the buffer.
+constexpr uint64_t kPoolKeepBytes = uint64_t(8) << 30;
+cudaError_t dev_alloc(void **p, uint64_t bytes, int *device);
+void dev_free(void *p, int device);
+
 // device buffer that owns its memory
 template <class T>
 struct DBuf {
   T *p = nullptr;
   uint64_t n = 0;
+  int dev = 0;
   cudaError_t alloc(uint64_t count) {
     release();
-    n = count;
     if (!count) return cudaSuccess;
-    return cudaMalloc(&p, count * sizeof(T));
+    const cudaError_t e = dev_alloc(reinterpret_cast<void **>(&p), count * sizeof(T), &dev);
+    if (e != cudaSuccess) p = nullptr;
+    n = p ? count : 0;
+    return e;
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) dev_free(p, dev);
     p = nullptr;
     n = 0;
   }

@@ -46,6 +46,75 @@ uint32_t *global_epoch(int device) {
   return d.d_global_epoch;
 }
 
+// The per-device memory pools behind dev_alloc: created on first use, with a
+// private stream that orders their allocations and frees (each is waited
+// for, so a buffer is usable on any stream when dev_alloc returns). Devices
+// without stream-ordered allocation fall back to cudaMalloc / cudaFree.
+struct DevPool {
+  std::once_flag once;
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t st = nullptr;
+};
+constexpr int kMaxPoolDevices = 64;
+DevPool g_pool[kMaxPoolDevices];
+
+DevPool *pool_of(int dev) {
+  if (dev < 0 || dev >= kMaxPoolDevices) return nullptr;
+  DevPool &P = g_pool[dev];
+  std::call_once(P.once, [&] {
+    int supported = 0;
+    if (cudaDeviceGetAttribute(&supported, cudaDevAttrMemoryPoolsSupported, dev) != cudaSuccess || !supported) return;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return;
+    uint64_t keep = kPoolKeepBytes;
+    cudaStream_t st = nullptr;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    const bool same = cur == dev || cudaSetDevice(dev) == cudaSuccess;
+    if (!same || cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      if (cur != dev) cudaSetDevice(cur);
+      return;
+    }
+    if (cur != dev) cudaSetDevice(cur);
+    P.pool = pool;
+    P.st = st;
+  });
+  return P.pool ? &P : nullptr;
+}
+
+cudaError_t dev_alloc(void **p, uint64_t bytes, int *device) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  *device = dev;
+  DevPool *P = pool_of(dev);
+  if (!P) return cudaMalloc(p, bytes);
+  e = cudaMallocFromPoolAsync(p, bytes, P->pool, P->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->st);
+  return e;
+}
+
+void dev_free(void *p, int device) {
+  DevPool *P = pool_of(device);
+  if (!P) {
+    cudaFree(p);
+    return;
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != device) cudaSetDevice(device);
+  cudaDeviceSynchronize();
+  cudaFreeAsync(p, P->st);
+  cudaStreamSynchronize(P->st);
+  if (cur != device) cudaSetDevice(cur);
+}
+
 }  // namespace aceapex
 
 
@@ -527,6 +596,18 @@ void aceapex_close(aceapex_archive *a) {
   cudaDeviceSynchronize();
   a->release();
   delete a;
+}
+
+int aceapex_release_cached_memory(int device) {
+  DevPool *P = pool_of(device);
+  if (!P) return ACEAPEX_OK;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != device && cudaSetDevice(device) != cudaSuccess) return ACEAPEX_ECUDA;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemPoolTrimTo(P->pool, 0);
+  if (cur != device) cudaSetDevice(cur);
+  return cuda_status(e);
 }
 
 uint64_t aceapex_decoded_size(const aceapex_archive *a) { return a ? a->h.n : 0; }

@@ -579,22 +579,8 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
       if (kMode == kViewPaged) bad |= V.page[q1] == 0xFFFFFFFFu;
       f1 = ld_acquire(A.flags + q1);
     }
-    if (__any_sync(kFull, bad)) {
-      ok = false;
-      break;
-    }
-    if (!__all_sync(kFull, f0 == epoch && f1 == epoch)) {
-      PHASE_COUNT(10, 1);
-      PHASE_MARK(3);
-      if (!wait_flags(A.flags + (need0 ? q0 : 0), need0, epoch, deadline, L.err, lane) ||
-          !wait_flags(A.flags + (need1 ? q1 : 0), need1, epoch, deadline, L.err, lane)) {
-        ok = false;
-        break;
-      }
-      PHASE_MARK(11);
-    }
-    PHASE_MARK(3);
-    PHASE_COUNT(6, 1);
+    // (the hazard ranges need no flag: they are found while the loads above
+    // are in flight, and the loaded values are used only after them)
     mt->src[lane] = src;
     mt->dst[lane] = dst;
     __syncwarp();
@@ -622,6 +608,22 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
       const uint32_t jlo = any_l ? jl + 1 : 0;
       if (any_h && jlo <= jh) hmask = ((2u << jh) - 1u) & ~((1u << jlo) - 1u);
     }
+    if (__any_sync(kFull, bad)) {
+      ok = false;
+      break;
+    }
+    if (!__all_sync(kFull, f0 == epoch && f1 == epoch)) {
+      PHASE_COUNT(10, 1);
+      PHASE_MARK(3);
+      if (!wait_flags(A.flags + (need0 ? q0 : 0), need0, epoch, deadline, L.err, lane) ||
+          !wait_flags(A.flags + (need1 ? q1 : 0), need1, epoch, deadline, L.err, lane)) {
+        ok = false;
+        break;
+      }
+      PHASE_MARK(11);
+    }
+    PHASE_MARK(3);
+    PHASE_COUNT(6, 1);
     bool pending = valid;
     for (int round = 0;; ++round) {
       const uint32_t pm = __ballot_sync(kFull, pending);
@@ -669,8 +671,10 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
             Y = *reinterpret_cast<const uint4 *>(pa - dl);
             cc = 16 + dl - o;
           }
+          // cc < 16 in both cases (dl, o < 16): the mask tells the compiler,
+          // which drops the selection level that a shift of 16 or more needs
           uint32_t r[4];
-          realign16(X, Y, cc, r);
+          realign16(X, Y, cc & 15u, r);
           uint8_t *to = out + b16;
           if (n == 16) {
             *reinterpret_cast<uint4 *>(to) = make_uint4(r[0], r[1], r[2], r[3]);
