@@ -679,18 +679,23 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
           if (n == 16) {
             *reinterpret_cast<uint4 *>(to) = make_uint4(r[0], r[1], r[2], r[3]);
           } else {
-            // bytes [o, o + n) of the block: whole words with one store,
-            // the (at most three) bytes at each end one by one
-#pragma unroll
-            for (uint32_t j = 0; j < 4; ++j) {
-              if (4 * j >= o && 4 * j + 4 <= o + n) {
-                *reinterpret_cast<uint32_t *>(to + 4 * j) = r[j];
-              } else if (4 * j + 4 > o && 4 * j < o + n) {
-#pragma unroll
-                for (uint32_t b = 0; b < 4; ++b)
-                  if (4 * j + b - o < n) to[4 * j + b] = (uint8_t)(r[j] >> (8 * b));
-              }
-            }
+            // bytes [o, o + n) of the block as naturally aligned pieces of
+            // 1, 2, 4 and 8 bytes, rising in size up to the first boundary
+            // that the next piece would cross, then falling: at most eight
+            // store instructions per warp for any mix of partial blocks (a
+            // scattered store costs the memory pipeline one pass per line
+            // it touches, whatever its width)
+            auto wd = [&](uint32_t i) { return i & 2 ? (i & 1 ? r[3] : r[2]) : (i & 1 ? r[1] : r[0]); };
+            uint32_t a = o;
+            const uint32_t e = o + n;
+            if ((a & 1) && a < e) { to[a] = (uint8_t)(wd(a >> 2) >> (8 * (a & 3))); a += 1; }
+            if ((a & 2) && a + 2 <= e) { *reinterpret_cast<uint16_t *>(to + a) = (uint16_t)(wd(a >> 2) >> (8 * (a & 2))); a += 2; }
+            if ((a & 4) && a + 4 <= e) { *reinterpret_cast<uint32_t *>(to + a) = wd(a >> 2); a += 4; }
+            if ((a & 8) && a + 8 <= e) { *reinterpret_cast<uint2 *>(to + a) = make_uint2(r[2], r[3]); a += 8; }
+            if (a + 8 <= e) { *reinterpret_cast<uint2 *>(to + a) = (a & 8) ? make_uint2(r[2], r[3]) : make_uint2(r[0], r[1]); a += 8; }
+            if (a + 4 <= e) { *reinterpret_cast<uint32_t *>(to + a) = wd(a >> 2); a += 4; }
+            if (a + 2 <= e) { *reinterpret_cast<uint16_t *>(to + a) = (uint16_t)(wd(a >> 2) >> (8 * (a & 2))); a += 2; }
+            if (a < e) to[a] = (uint8_t)(wd(a >> 2) >> (8 * (a & 3)));
           }
         } else {
           const uint32_t o = (uu - mt->start[m]) << 4;
