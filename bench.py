@@ -511,14 +511,16 @@ RANS_STEP_OPS = 27
 
 def workload_entropy(args):
     """The entropy stage alone: a literal-only archive (no matches) of
-    back-to-back FASTQ quality strings, 4,096 streams of 64 KiB by default, each
-    16 KiB segment one 32-lane interleaved rANS message of 16,384 symbols."""
+    back-to-back FASTQ quality strings, 16,384 streams of 64 KiB (1 GiB, the
+    size of the FASTQ workload) by default, each 16 KiB segment one 32-lane
+    interleaved rANS message of 16,384 symbols. (At 256 MiB a launch holds
+    only 3.4 segments per warp, and the launch's tail weighs on the rate.)"""
     import torch
 
     import paper_2606_18900_gb300 as ace
     import synth
 
-    size = args.size or 4096 * 65536
+    size = args.size or 16384 * 65536
     data = synth.qualities(size)
     t = time.perf_counter()
     arc_bytes = ace.encode(data, log2_B=args.log2_block, min_match=255)
