@@ -285,7 +285,7 @@ int aceapex_server_get_stats(aceapex_server *s, aceapex_server_stats *out);
  * Scratch: a fixed array of about 4.3 MiB in the library's device memory,
  * which every GPU that loads the library holds until the process exits. The
  * first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture. Archives
+ * device current). Archives
  * of more than 65,536 segments (1 GiB at 16 KiB segments) are rejected with
  * ERANGE. All calls share the array and it keeps the last call's contents;
  * each call resets what must start at zero, but calls that overlap on the
