@@ -172,6 +172,7 @@ def lib():
             L.aceapex_fastq_index.argtypes = [vp, u64, u64p, u64]
             L.aceapex_fastq_index.restype = u64
             L.aceapex_decode_all_to_host.argtypes = [vp, vp, u64, u64, vp]
+            L.aceapex_decode_host.argtypes = [vp, u64, i32, vp, u64, u64]
             L.aceapex_fastq_split.argtypes = [vp, u64, vp, u64p]
             L.aceapex_fastq_split.restype = u64
             L.aceapex_decode_fastq_streams.argtypes = [ctypes.POINTER(vp), vp, u64, vp]
@@ -313,6 +314,17 @@ def fastq_index(data) -> np.ndarray:
     out = np.zeros(max(n, 1), dtype=np.uint64)
     L.aceapex_fastq_index(buf.ctypes.data, buf.size, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), n)
     return out[:n]
+
+
+def decode_host(archive, out, device: int = 0, window: int = 0):
+    """Decode a host archive (numpy array or CPU tensor; pinned memory lets
+    its upload overlap) into host memory `out` (CPU tensor or numpy array of
+    at least the decoded size) in one call: aceapex_decode_host (open, upload
+    overlapped with the window decodes and copies back, close)."""
+    nbytes = archive.nbytes if isinstance(archive, np.ndarray) else archive.numel() * archive.element_size()
+    cap = out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()
+    _check(lib().aceapex_decode_host(_ptr(archive), nbytes, int(device), _ptr(out), cap, window),
+           "aceapex_decode_host")
 
 
 def release_cached_memory(device: int = 0):

@@ -171,6 +171,11 @@ struct aceapex_archive {
   uint64_t win_bytes = 0;
   cudaStream_t copy_st = nullptr;
   std::vector<cudaEvent_t> win_ev;
+  // a payload upload still in flight after the open (aceapex_decode_host):
+  // its stream, an event after each piece and the payload bytes then present
+  cudaStream_t up_st = nullptr;
+  std::vector<cudaEvent_t> up_ev;
+  std::vector<uint64_t> up_end;
   // FASTQ stream reassembly (when this handle is a set's first part)
   DBuf<uint8_t> d_fq_streams;
   DBuf<uint32_t> d_fq_counts, d_fq_nl;
@@ -197,7 +202,17 @@ struct aceapex_archive {
     return A;
   }
 
+  void end_upload() {
+    if (up_st) cudaStreamSynchronize(up_st);
+    for (cudaEvent_t e : up_ev) cudaEventDestroy(e);
+    up_ev.clear();
+    up_end.clear();
+    if (up_st) cudaStreamDestroy(up_st);
+    up_st = nullptr;
+  }
+
   void release() {
+    end_upload();
     d_payload.release(); d_dir.release(); d_lut.release(); d_flags.release(); d_order.release();
     d_words.release(); d_blocked.release(); d_scratch.release(); d_page.release(); d_arena.release();
     d_work.release(); d_ring.release(); d_seg_crc.release(); d_batch_arcs.release(); d_batch_views.release();

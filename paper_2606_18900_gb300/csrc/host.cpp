@@ -522,7 +522,18 @@ int decode_closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, cudaStream_
 
 extern "C" {
 
-int aceapex_open(const void *h_archive, uint64_t nbytes, int device, aceapex_archive **out) {
+}  // extern "C"
+
+namespace aceapex {
+
+// Payload pieces of an upload that decoding may overtake (aceapex_decode_host).
+constexpr uint64_t kUploadPiece = uint64_t(32) << 20;
+
+// aceapex_open; with keep_upload the payload goes up in pieces, each followed
+// by an event, and the open returns while they are in flight (the handle's
+// up_st / up_ev / up_end): the caller must keep the host bytes until the
+// handle is closed, and a decode must wait for the pieces it reads.
+int open_archive(const void *h_archive, uint64_t nbytes, int device, aceapex_archive **out, bool keep_upload) {
   if (!h_archive || !out || nbytes == 0) return ACEAPEX_EINVAL;
   *out = nullptr;
   aceapex_archive *A = new (std::nothrow) aceapex_archive();
@@ -542,12 +553,33 @@ int aceapex_open(const void *h_archive, uint64_t nbytes, int device, aceapex_arc
   cudaStream_t up = nullptr;
   bool uploading = false;
   if (dev_ok && pay_bytes && cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking) == cudaSuccess &&
-      A->d_payload.alloc(pay_bytes) == cudaSuccess &&
-      cudaMemcpyAsync(A->d_payload.p, a + pay_off, pay_bytes, cudaMemcpyHostToDevice, up) == cudaSuccess)
+      A->d_payload.alloc(pay_bytes) == cudaSuccess) {
     uploading = true;
+    if (!keep_upload) {
+      uploading = cudaMemcpyAsync(A->d_payload.p, a + pay_off, pay_bytes, cudaMemcpyHostToDevice, up) == cudaSuccess;
+    } else {
+      A->up_st = up;
+      for (uint64_t o = 0; uploading && o < pay_bytes; o += kUploadPiece) {
+        const uint64_t n = std::min(kUploadPiece, pay_bytes - o);
+        cudaEvent_t ev = nullptr;
+        uploading = cudaMemcpyAsync(A->d_payload.p + o, a + pay_off + o, n, cudaMemcpyHostToDevice, up) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+        if (ev) {
+          A->up_ev.push_back(ev);
+          A->up_end.push_back(o + n);
+          uploading = uploading && cudaEventRecord(ev, up) == cudaSuccess;
+        }
+      }
+    }
+  }
   int rc = validate(a, nbytes, A);
-  const bool upload_ok = !uploading || cudaStreamSynchronize(up) == cudaSuccess;
-  if (up) cudaStreamDestroy(up);
+  const bool wait_now = !keep_upload || rc || !uploading || !dev_ok;
+  const bool upload_ok = !uploading || !wait_now || cudaStreamSynchronize(up) == cudaSuccess;
+  if (wait_now) {
+    A->end_upload();  // (also destroys up when the handle took it)
+    if (up && !keep_upload) cudaStreamDestroy(up);
+    up = nullptr;
+  }
   if (rc || !upload_ok || !dev_ok) {
     A->release();
     delete A;
@@ -561,6 +593,7 @@ int aceapex_open(const void *h_archive, uint64_t nbytes, int device, aceapex_arc
   // (the payload buffer is the uploaded one when the header's payload fields
   // were what validation accepted, else it is allocated and copied now)
   const bool have_payload = uploading && pay_off == h.off_payload && pay_bytes == h.payload_bytes;
+  if (!have_payload) A->end_upload();
   bool okm = (have_payload || A->d_payload.alloc(std::max<uint64_t>(h.payload_bytes, 16)) == cudaSuccess) &&
              A->d_dir.alloc(std::max<uint64_t>(h.n_seg, 1)) == cudaSuccess &&
              A->d_lut.alloc(4 * kScale) == cudaSuccess && A->d_flags.alloc(std::max<uint64_t>(h.n_seg, 1)) == cudaSuccess &&
@@ -588,6 +621,14 @@ int aceapex_open(const void *h_archive, uint64_t nbytes, int device, aceapex_arc
   }
   *out = A;
   return ACEAPEX_OK;
+}
+
+}  // namespace aceapex
+
+extern "C" {
+
+int aceapex_open(const void *h_archive, uint64_t nbytes, int device, aceapex_archive **out) {
+  return open_archive(h_archive, nbytes, device, out, false);
 }
 
 void aceapex_close(aceapex_archive *a) {
@@ -704,6 +745,17 @@ int aceapex_decode_all_to_host(aceapex_archive *a, void *h_out, uint64_t out_cap
     if (e != cudaSuccess) break;
     L.work = a->d_win_work.p + a->win_start[k];
     L.n_work = (uint32_t)(a->win_start[k + 1] - a->win_start[k]);
+    if (!a->up_ev.empty()) {
+      // a payload upload still in flight: wait for the piece that completes
+      // this window's payload (segments are laid out in order; the last one's
+      // words end the window's part)
+      const uint64_t s_last = std::min<uint64_t>(a->h.n_seg, (k + 1) * window / S + ((k + 1) * window % S ? 1 : 0)) - 1;
+      const SegRec &r = a->dir[s_last];
+      const uint64_t need = (r.payload_off + 128 + 2 * (uint64_t)r.n_words + 15) & ~uint64_t(15);
+      size_t i = 0;
+      while (i + 1 < a->up_end.size() && a->up_end[i] < need) ++i;
+      if ((e = cudaStreamWaitEvent(st, a->up_ev[i], 0)) != cudaSuccess) break;
+    }
     if ((e = launch_decode(L, a->grid, kBlock, st)) != cudaSuccess) break;
     if ((e = cudaEventRecord(a->win_ev[k], st)) != cudaSuccess) break;
     if ((e = cudaStreamWaitEvent(a->copy_st, a->win_ev[k], 0)) != cudaSuccess) break;
@@ -714,6 +766,25 @@ int aceapex_decode_all_to_host(aceapex_archive *a, void *h_out, uint64_t out_cap
   if (e == cudaSuccess) e = cudaEventRecord(a->win_ev[nwin], a->copy_st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st, a->win_ev[nwin], 0);
   return cuda_status(e);
+}
+
+int aceapex_decode_host(const void *h_archive, uint64_t nbytes, int device, void *h_out, uint64_t out_cap,
+                        uint64_t window) {
+  if (!h_archive || nbytes == 0) return ACEAPEX_EINVAL;
+  aceapex_archive *A = nullptr;
+  int rc = open_archive(h_archive, nbytes, device, &A, true);
+  if (rc) return rc;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    aceapex_close(A);
+    return ACEAPEX_ECUDA;
+  }
+  rc = aceapex_decode_all_to_host(A, h_out, out_cap, window, st);
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (!rc) rc = e == cudaSuccess ? aceapex_last_error(A, 0, nullptr) : ACEAPEX_ECUDA;
+  cudaStreamDestroy(st);
+  aceapex_close(A);
+  return rc;
 }
 
 int aceapex_decode_range(aceapex_archive *a, uint64_t lo, uint64_t hi, void *d_out, uint64_t out_cap, void *stream) {

@@ -259,6 +259,33 @@ def test_decode_all_to_host_windows(window):
             assert_same(host.numpy(), d)
 
 
+@pytest.mark.parametrize("window", [0, 1 << 20, 16384])
+def test_decode_host_one_call(window):
+    """aceapex_decode_host: host archive in, host output out, in one call,
+    equal to the source; a short output buffer is ERANGE, a damaged header
+    ECORRUPT (host validation) and a damaged payload ECORRUPT (the decode's
+    own checks), each without a fault."""
+    d = synth.pe_fastq(8 << 20, ref_len=2_000_000)
+    a = ace.encode(d, min_match=16)
+    host = torch.zeros(d.size, dtype=torch.uint8).pin_memory()
+    ace.decode_host(torch.from_numpy(a).pin_memory(), host, window=window)
+    assert_same(host.numpy(), d)
+    with pytest.raises(ace.AceapexError) as e:
+        ace.decode_host(a, torch.zeros(d.size - 1, dtype=torch.uint8))
+    assert e.value.code == ace.ERANGE
+    bad = a.copy()
+    bad[0] ^= 1
+    with pytest.raises(ace.AceapexError) as e:
+        ace.decode_host(bad, host)
+    assert e.value.code == ace.ECORRUPT
+    bad = a.copy()
+    off = oracle.sections(a)["off_payload"]
+    bad[off:off + 4] = 0  # the first segment's first state below 2^16
+    with pytest.raises(ace.AceapexError) as e:
+        ace.decode_host(bad, host)
+    assert e.value.code == ace.ECORRUPT
+
+
 def test_level_counts_match_directory():
     d = synth.pe_fastq(2 << 20, ref_len=500_000)
     a = ace.encode(d, min_match=12, max_level=5)

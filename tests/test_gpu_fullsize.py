@@ -35,6 +35,13 @@ def test_fullsize_fastq(fastq_1g, log2_B):
     assert got.size == d.size
     assert np.array_equal(got, d)
     if log2_B == 14:
+        # one call from the pinned host archive to pinned host output: the
+        # payload (about 400 MB, 13 pieces) is uploaded while the windows
+        # decode and are copied back
+        h_arc = torch.from_numpy(a).pin_memory()
+        host = torch.zeros(d.size, dtype=torch.uint8).pin_memory()
+        ace.decode_host(h_arc, host)
+        assert np.array_equal(host.numpy(), d)
         want = oracle.decode(a)
         rng = np.random.default_rng(0)
         S = 1 << 14
