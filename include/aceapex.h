@@ -122,13 +122,15 @@ int aceapex_decode_all_to_host(aceapex_archive *a, void *h_out, uint64_t out_cap
 
 /*
  * One call from a host archive to host output (paper §3.3's end-to-end
- * path): open the archive on `device` (host validation as in aceapex_open),
- * decode it as aceapex_decode_all_to_host does, check the decode's error
- * word and close the handle, returning when h_out[0..N) holds the output.
- * Unlike open followed by a decode, the payload goes to the device in 32 MiB
- * pieces that decoding may overtake: a window's decode starts once the
- * pieces holding its segments have arrived, so the upload, the decodes and
- * the copies back overlap. h_archive (nbytes, caller-owned, read only; pinned
+ * path): open the archive on `device`, decode it as
+ * aceapex_decode_all_to_host does, check the decode's error word and close
+ * the handle, returning when h_out[0..N) holds the output. The host checks
+ * are aceapex_open's without the dependency lists and the read index, which
+ * a whole-file decode does not read. Unlike open followed by a decode, the
+ * payload goes to the device last, in 32 MiB pieces that decoding may
+ * overtake: a window's decode starts once the pieces holding its segments
+ * have arrived, so the upload, the decodes and the copies back overlap.
+ * h_archive (nbytes, caller-owned, read only; pinned
  * memory for the upload to overlap) is read until the call returns. Errors:
  * those of aceapex_open and aceapex_decode_all_to_host, and the device-side
  * ECORRUPT / ETIMEOUT of the decode.

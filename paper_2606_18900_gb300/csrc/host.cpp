@@ -140,7 +140,11 @@ void parallel_for(uint64_t n, F f) {
   for (auto &t : ts) t.join();
 }
 
-int validate(const uint8_t *a, uint64_t len, aceapex_archive *A) {
+int fill_stats(aceapex_archive *A, uint64_t n_lit, uint64_t n_cmd, uint32_t max_lv);
+
+// (lists = false: the dependency lists and the read index are neither checked
+// nor copied; a whole-file decode reads neither)
+int validate(const uint8_t *a, uint64_t len, aceapex_archive *A, bool lists = true) {
   if (len < kHeaderBytes + kTablesBytes || std::memcmp(a, "ACEAPEX1", 8) != 0) return ACEAPEX_ECORRUPT;
   if (rd<uint32_t>(a + 8) != 1 || rd<uint32_t>(a + 12) != kHeaderBytes) return ACEAPEX_ECORRUPT;
   Header &h = A->h;
@@ -201,6 +205,7 @@ int validate(const uint8_t *a, uint64_t len, aceapex_archive *A) {
     max_lv = std::max<uint32_t>(max_lv, r.level);
   }
   if (po != h.payload_bytes) return ACEAPEX_ECORRUPT;
+  if (!lists) return fill_stats(A, n_lit, n_cmd, max_lv);
   // dependency lists (ascending, below their segment, level consistent) and
   // the read index (ascending, below N): copied and checked in parallel
   // pieces, since at gigabyte sizes these are millions of entries
@@ -253,7 +258,11 @@ int validate(const uint8_t *a, uint64_t len, aceapex_archive *A) {
   });
   for (uint8_t b : bad)
     if (b) return ACEAPEX_ECORRUPT;
+  return fill_stats(A, n_lit, n_cmd, max_lv);
+}
 
+int fill_stats(aceapex_archive *A, uint64_t n_lit, uint64_t n_cmd, uint32_t max_lv) {
+  const Header &h = A->h;
   aceapex_stats &st = A->stats;
   st.decoded_bytes = h.n;
   st.compressed_bytes = h.payload_bytes + 24 * h.n_seg + kTablesBytes;
@@ -529,11 +538,12 @@ namespace aceapex {
 // Payload pieces of an upload that decoding may overtake (aceapex_decode_host).
 constexpr uint64_t kUploadPiece = uint64_t(32) << 20;
 
-// aceapex_open; with keep_upload the payload goes up in pieces, each followed
-// by an event, and the open returns while they are in flight (the handle's
-// up_st / up_ev / up_end): the caller must keep the host bytes until the
-// handle is closed, and a decode must wait for the pieces it reads.
-int open_archive(const void *h_archive, uint64_t nbytes, int device, aceapex_archive **out, bool keep_upload) {
+// aceapex_open. With defer_payload (aceapex_decode_host) the host checks
+// leave out the dependency lists and the read index, which a whole-file
+// decode does not read, and the payload is not copied: start_payload_upload
+// copies it afterwards, once the small sections are on the device, so that
+// their copies do not queue behind it.
+int open_archive(const void *h_archive, uint64_t nbytes, int device, aceapex_archive **out, bool defer_payload) {
   if (!h_archive || !out || nbytes == 0) return ACEAPEX_EINVAL;
   *out = nullptr;
   aceapex_archive *A = new (std::nothrow) aceapex_archive();
@@ -552,34 +562,13 @@ int open_archive(const void *h_archive, uint64_t nbytes, int device, aceapex_arc
   }
   cudaStream_t up = nullptr;
   bool uploading = false;
-  if (dev_ok && pay_bytes && cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking) == cudaSuccess &&
-      A->d_payload.alloc(pay_bytes) == cudaSuccess) {
+  if (!defer_payload && dev_ok && pay_bytes && cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking) == cudaSuccess &&
+      A->d_payload.alloc(pay_bytes) == cudaSuccess &&
+      cudaMemcpyAsync(A->d_payload.p, a + pay_off, pay_bytes, cudaMemcpyHostToDevice, up) == cudaSuccess)
     uploading = true;
-    if (!keep_upload) {
-      uploading = cudaMemcpyAsync(A->d_payload.p, a + pay_off, pay_bytes, cudaMemcpyHostToDevice, up) == cudaSuccess;
-    } else {
-      A->up_st = up;
-      for (uint64_t o = 0; uploading && o < pay_bytes; o += kUploadPiece) {
-        const uint64_t n = std::min(kUploadPiece, pay_bytes - o);
-        cudaEvent_t ev = nullptr;
-        uploading = cudaMemcpyAsync(A->d_payload.p + o, a + pay_off + o, n, cudaMemcpyHostToDevice, up) == cudaSuccess &&
-                    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
-        if (ev) {
-          A->up_ev.push_back(ev);
-          A->up_end.push_back(o + n);
-          uploading = uploading && cudaEventRecord(ev, up) == cudaSuccess;
-        }
-      }
-    }
-  }
-  int rc = validate(a, nbytes, A);
-  const bool wait_now = !keep_upload || rc || !uploading || !dev_ok;
-  const bool upload_ok = !uploading || !wait_now || cudaStreamSynchronize(up) == cudaSuccess;
-  if (wait_now) {
-    A->end_upload();  // (also destroys up when the handle took it)
-    if (up && !keep_upload) cudaStreamDestroy(up);
-    up = nullptr;
-  }
+  int rc = validate(a, nbytes, A, !defer_payload);
+  const bool upload_ok = !uploading || cudaStreamSynchronize(up) == cudaSuccess;
+  if (up) cudaStreamDestroy(up);
   if (rc || !upload_ok || !dev_ok) {
     A->release();
     delete A;
@@ -593,7 +582,6 @@ int open_archive(const void *h_archive, uint64_t nbytes, int device, aceapex_arc
   // (the payload buffer is the uploaded one when the header's payload fields
   // were what validation accepted, else it is allocated and copied now)
   const bool have_payload = uploading && pay_off == h.off_payload && pay_bytes == h.payload_bytes;
-  if (!have_payload) A->end_upload();
   bool okm = (have_payload || A->d_payload.alloc(std::max<uint64_t>(h.payload_bytes, 16)) == cudaSuccess) &&
              A->d_dir.alloc(std::max<uint64_t>(h.n_seg, 1)) == cudaSuccess &&
              A->d_lut.alloc(4 * kScale) == cudaSuccess && A->d_flags.alloc(std::max<uint64_t>(h.n_seg, 1)) == cudaSuccess &&
@@ -605,7 +593,7 @@ int open_archive(const void *h_archive, uint64_t nbytes, int device, aceapex_arc
     return ACEAPEX_ENOMEM;
   }
   cudaError_t e = cudaSuccess;
-  if (h.payload_bytes && !have_payload)
+  if (h.payload_bytes && !have_payload && !defer_payload)
     e = cudaMemcpy(A->d_payload.p, a + h.off_payload, h.payload_bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && h.n_seg) e = cudaMemcpy(A->d_dir.p, A->dir.data(), 24 * h.n_seg, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(A->d_lut.p, lut.data(), 4 * lut.size(), cudaMemcpyHostToDevice);
@@ -620,6 +608,69 @@ int open_archive(const void *h_archive, uint64_t nbytes, int device, aceapex_arc
     return ACEAPEX_ECUDA;
   }
   *out = A;
+  return ACEAPEX_OK;
+}
+
+// The payload of a handle opened with defer_payload, in pieces on the
+// handle's upload stream, each followed by an event (up_ev / up_end).
+int start_payload_upload(aceapex_archive *A, const void *h_archive) {
+  const Header &h = A->h;
+  if (!h.payload_bytes) return ACEAPEX_OK;
+  if (cudaStreamCreateWithFlags(&A->up_st, cudaStreamNonBlocking) != cudaSuccess) return ACEAPEX_ECUDA;
+  const uint8_t *src = static_cast<const uint8_t *>(h_archive) + h.off_payload;
+  for (uint64_t o = 0; o < h.payload_bytes; o += kUploadPiece) {
+    const uint64_t n = std::min(kUploadPiece, h.payload_bytes - o);
+    cudaEvent_t ev = nullptr;
+    if (cudaMemcpyAsync(A->d_payload.p + o, src + o, n, cudaMemcpyHostToDevice, A->up_st) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+      return ACEAPEX_ECUDA;
+    A->up_ev.push_back(ev);
+    A->up_end.push_back(o + n);
+    if (cudaEventRecord(ev, A->up_st) != cudaSuccess) return ACEAPEX_ECUDA;
+  }
+  return ACEAPEX_OK;
+}
+
+
+// What a decode to host memory needs besides the archive, for windows of
+// `window` bytes (a multiple of the segment size): scratch, the device
+// output buffer, the copy stream, the windows' work lists in level order
+// (built once per window size) and their events.
+int prepare_windows(aceapex_archive *a, uint64_t window, cudaStream_t st) {
+  const uint64_t S = uint64_t(1) << a->h.log2_S;
+  int rc = ensure_scratch(a);
+  if (rc) return rc;
+  if (a->d_host_out.n < a->h.n) {
+    cudaStreamSynchronize(st);
+    if (a->d_host_out.alloc(a->h.n) != cudaSuccess) return ACEAPEX_ENOMEM;
+  }
+  if (!a->copy_st && cudaStreamCreateWithFlags(&a->copy_st, cudaStreamNonBlocking) != cudaSuccess)
+    return ACEAPEX_ECUDA;
+  if (a->win_bytes != window) {
+    cudaStreamSynchronize(st);
+    std::vector<WorkItem> work;
+    std::vector<uint32_t> segs;
+    a->win_start.clear();
+    for (uint64_t lo = 0; lo < a->h.n; lo += window) {
+      segs.clear();
+      const uint64_t s1 = std::min(a->h.n_seg, (lo + window) / S + ((lo + window) % S ? 1 : 0));
+      for (uint64_t s = lo / S; s < s1; ++s) segs.push_back((uint32_t)s);
+      a->win_start.push_back(work.size());
+      level_order(a->dir, segs.data(), segs.size(), 0, work);
+    }
+    a->win_start.push_back(work.size());
+    if (a->d_win_work.alloc(work.size()) != cudaSuccess ||
+        cudaMemcpy(a->d_win_work.p, work.data(), sizeof(WorkItem) * work.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+      return ACEAPEX_ENOMEM;
+    a->win_bytes = window;
+  }
+  const size_t nwin = a->win_start.size() - 1;
+  while (a->win_ev.size() < nwin + 1) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return ACEAPEX_ECUDA;
+    a->win_ev.push_back(e);
+  }
   return ACEAPEX_OK;
 }
 
@@ -695,41 +746,10 @@ int aceapex_decode_all_to_host(aceapex_archive *a, void *h_out, uint64_t out_cap
   if (window == 0) window = uint64_t(256) << 20;
   window = std::max<uint64_t>(S, window / S * S);
   if (cudaSetDevice(a->device) != cudaSuccess) return ACEAPEX_ECUDA;
-  int rc = ensure_scratch(a);
-  if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (a->d_host_out.n < a->h.n) {
-    cudaStreamSynchronize(st);
-    if (a->d_host_out.alloc(a->h.n) != cudaSuccess) return ACEAPEX_ENOMEM;
-  }
-  if (!a->copy_st && cudaStreamCreateWithFlags(&a->copy_st, cudaStreamNonBlocking) != cudaSuccess)
-    return ACEAPEX_ECUDA;
-  // work lists of the windows, each in level order (built once per window size)
-  if (a->win_bytes != window) {
-    cudaStreamSynchronize(st);
-    std::vector<WorkItem> work;
-    std::vector<uint32_t> segs;
-    a->win_start.clear();
-    for (uint64_t lo = 0; lo < a->h.n; lo += window) {
-      segs.clear();
-      const uint64_t s1 = std::min(a->h.n_seg, (lo + window) / S + ((lo + window) % S ? 1 : 0));
-      for (uint64_t s = lo / S; s < s1; ++s) segs.push_back((uint32_t)s);
-      a->win_start.push_back(work.size());
-      level_order(a->dir, segs.data(), segs.size(), 0, work);
-    }
-    a->win_start.push_back(work.size());
-    if (a->d_win_work.alloc(work.size()) != cudaSuccess ||
-        cudaMemcpy(a->d_win_work.p, work.data(), sizeof(WorkItem) * work.size(), cudaMemcpyHostToDevice) !=
-            cudaSuccess)
-      return ACEAPEX_ENOMEM;
-    a->win_bytes = window;
-  }
+  int rc = prepare_windows(a, window, st);
+  if (rc) return rc;
   const size_t nwin = a->win_start.size() - 1;
-  while (a->win_ev.size() < nwin + 1) {
-    cudaEvent_t e;
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return ACEAPEX_ECUDA;
-    a->win_ev.push_back(e);
-  }
   uint32_t *ge = global_epoch(a->device);
   if (!ge) return ACEAPEX_ECUDA;
   // the copy stream starts after the caller's earlier work
@@ -774,12 +794,21 @@ int aceapex_decode_host(const void *h_archive, uint64_t nbytes, int device, void
   aceapex_archive *A = nullptr;
   int rc = open_archive(h_archive, nbytes, device, &A, true);
   if (rc) return rc;
+  if (!h_out && A->h.n) rc = ACEAPEX_EINVAL;
+  else if (out_cap < A->h.n) rc = ACEAPEX_ERANGE;
   cudaStream_t st = nullptr;
-  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+  if (!rc && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) rc = ACEAPEX_ECUDA;
+  if (rc) {
     aceapex_close(A);
-    return ACEAPEX_ECUDA;
+    return rc;
   }
-  rc = aceapex_decode_all_to_host(A, h_out, out_cap, window, st);
+  // everything the windows need goes to the device before the payload, whose
+  // pieces the window decodes then follow
+  const uint64_t S = uint64_t(1) << A->h.log2_S;
+  const uint64_t win = std::max<uint64_t>(S, (window ? window : uint64_t(256) << 20) / S * S);
+  if (A->h.n) rc = prepare_windows(A, win, st);
+  if (!rc) rc = start_payload_upload(A, h_archive);
+  if (!rc) rc = aceapex_decode_all_to_host(A, h_out, out_cap, window, st);
   const cudaError_t e = cudaStreamSynchronize(st);
   if (!rc) rc = e == cudaSuccess ? aceapex_last_error(A, 0, nullptr) : ACEAPEX_ECUDA;
   cudaStreamDestroy(st);
