@@ -110,7 +110,7 @@ int aceapex_decode_all(aceapex_archive *a, void *d_out, uint64_t out_cap, void *
 /*
  * Whole-file decode into host memory (paper §3.3's end-to-end measurement
  * over the host link): the archive decodes into a device buffer owned by the
- * handle, in windows of `window` bytes (0: 256 MiB; rounded to whole
+ * handle, in windows of `window` bytes (0: 64 MiB; rounded to whole
  * segments) taken in order, and each window is copied to h_out[0..N) on a
  * second stream while the next one decodes. A window's segments read only
  * segments of the same or earlier windows, which are complete by then.

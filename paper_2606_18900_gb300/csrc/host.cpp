@@ -312,7 +312,15 @@ void level_order(const std::vector<SegRec> &dir, const uint32_t *segs, uint64_t 
 // when the archive (or, for a batch, any archive) has such a segment.
 int ensure_scratch(aceapex_archive *A, uint32_t need_cmd_syms) {
   if (!A->max_grid) {
-    A->max_grid = decode_grid(A->device, kBlock);
+    // (looked up once per device: the lookup sets kernel attributes and asks
+    // the driver for the occupancy, and every open needs it)
+    static std::mutex grid_mu;
+    static std::map<int, int> grid_of;
+    {
+      std::lock_guard<std::mutex> lk(grid_mu);
+      auto it = grid_of.find(A->device);
+      A->max_grid = it != grid_of.end() ? it->second : (grid_of[A->device] = decode_grid(A->device, kBlock));
+    }
     if (A->grid <= 0 || A->grid > A->max_grid) A->grid = A->max_grid;
     A->scratch_warps = (uint32_t)A->max_grid * (kBlock / 32);
   }
@@ -537,6 +545,9 @@ namespace aceapex {
 
 // Payload pieces of an upload that decoding may overtake (aceapex_decode_host).
 constexpr uint64_t kUploadPiece = uint64_t(32) << 20;
+// Default window of a decode to host memory: the first window's decode is
+// all that precedes the first copy back, so windows are kept short.
+constexpr uint64_t kHostWindow = uint64_t(64) << 20;
 
 // aceapex_open. With defer_payload (aceapex_decode_host) the host checks
 // leave out the dependency lists and the read index, which a whole-file
@@ -551,9 +562,10 @@ int open_archive(const void *h_archive, uint64_t nbytes, int device, aceapex_arc
   const uint8_t *a = static_cast<const uint8_t *>(h_archive);
   A->device = device;
   const bool dev_ok = cudaSetDevice(device) == cudaSuccess;  // reported after validation
-  // The payload (almost all of the archive) goes to the device while the
-  // host checks the rest: its place and size come from the header, checked
-  // against the buffer size first; the copy is waited for before any return.
+  // Unless deferred, the payload (almost all of the archive) goes to the
+  // device while the host checks the rest: its place and size come from the
+  // header, checked against the buffer size first; the copy is waited for
+  // before any return.
   uint64_t pay_off = 0, pay_bytes = 0;
   if (nbytes >= kHeaderBytes) {
     pay_off = rd<uint64_t>(a + 104);
@@ -743,7 +755,7 @@ int aceapex_decode_all_to_host(aceapex_archive *a, void *h_out, uint64_t out_cap
   if (out_cap < a->h.n) return ACEAPEX_ERANGE;
   if (a->h.n == 0) return ACEAPEX_OK;
   const uint64_t S = uint64_t(1) << a->h.log2_S;
-  if (window == 0) window = uint64_t(256) << 20;
+  if (window == 0) window = kHostWindow;
   window = std::max<uint64_t>(S, window / S * S);
   if (cudaSetDevice(a->device) != cudaSuccess) return ACEAPEX_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -805,7 +817,7 @@ int aceapex_decode_host(const void *h_archive, uint64_t nbytes, int device, void
   // everything the windows need goes to the device before the payload, whose
   // pieces the window decodes then follow
   const uint64_t S = uint64_t(1) << A->h.log2_S;
-  const uint64_t win = std::max<uint64_t>(S, (window ? window : uint64_t(256) << 20) / S * S);
+  const uint64_t win = std::max<uint64_t>(S, (window ? window : kHostWindow) / S * S);
   if (A->h.n) rc = prepare_windows(A, win, st);
   if (!rc) rc = start_payload_upload(A, h_archive);
   if (!rc) rc = aceapex_decode_all_to_host(A, h_out, out_cap, window, st);
