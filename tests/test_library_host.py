@@ -213,3 +213,28 @@ def test_open_rejects_damaged_archives():
         assert _open_status(b) == ace.ECORRUPT
     lib = ace.lib()
     assert lib.aceapex_open(None, 10, 0, ctypes.byref(ctypes.c_void_p())) == ace.EINVAL
+
+
+def test_decode_host_host_checks():
+    """aceapex_decode_host runs the host checks before any device work: a
+    null or empty archive is EINVAL and a damaged header or table ECORRUPT
+    (without a GPU the checks still run; a sound archive then fails with
+    ECUDA or decodes)."""
+    lib = ace.lib()
+    a = ace.encode(synth.tiny_fastq()[:200_000], min_match=16)
+    out = np.zeros(200_000, np.uint8)
+
+    def status(buf):
+        b = np.ascontiguousarray(buf, dtype=np.uint8)
+        return lib.aceapex_decode_host(b.ctypes.data, b.size, 0, out.ctypes.data, out.size, 0)
+
+    assert lib.aceapex_decode_host(None, 10, 0, out.ctypes.data, out.size, 0) == ace.EINVAL
+    assert lib.aceapex_decode_host(a.ctypes.data, 0, 0, out.ctypes.data, out.size, 0) == ace.EINVAL
+    for off, val in [(0, 0), (8, 2), (26, 7), (40, 99)]:
+        b = a.copy()
+        b[off] = val
+        assert status(b) == ace.ECORRUPT, off
+    b = a.copy()
+    b[128 + 1] ^= 4          # table sum
+    assert status(b) == ace.ECORRUPT
+    assert status(a) in (ace.OK, ace.ECUDA)
