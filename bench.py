@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--size", type=int, default=0, help="workload bytes (0 = the workload's default)")
     p.add_argument("--min-match", type=int, default=0, help="0 = the workload's default")
     p.add_argument("--reads", type=int, default=200, help="random reads timed (fastq)")
+    p.add_argument("--max-level", type=int, default=8, help="fastq: the encoder's dependency-level cap")
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--batch-max", type=int, default=1 << 24)
     p.add_argument("--ring", type=int, default=4 << 30)
@@ -234,17 +235,17 @@ def max_over_ranks(value, world, device="cpu"):
     return float(t.item())
 
 
-def make_fastq(size, log2_block, min_match, rank, world):
+def make_fastq(size, log2_block, min_match, rank, world, max_level=8):
     """The paired-end FASTQ workload encoded by the library encoder; with
     several ranks, one replica shared through /dev/shm."""
     import paper_2606_18900_gb300 as ace
     import synth
 
     data = synth.pe_fastq(size)
-    path = f"/dev/shm/aceapex_bench_{size}_{log2_block}_{min_match}.bin"
+    path = f"/dev/shm/aceapex_bench_{size}_{log2_block}_{min_match}_{max_level}.bin"
     arc, enc_s = shared_archive(
-        lambda: ace.encode(data, log2_B=log2_block, min_match=min_match, reads=ace.fastq_index(data)), path, rank,
-        world)
+        lambda: ace.encode(data, log2_B=log2_block, min_match=min_match, max_level=max_level,
+                           reads=ace.fastq_index(data)), path, rank, world)
     return data, arc, enc_s
 
 
@@ -275,6 +276,38 @@ def random_reads(arc, data, n, seed, stream, device):
                "segments_p50": pctl(segs, 50), "segments_p99": pctl(segs, 99), "segments_max": max(segs) if segs else None,
                "depth_p50": pctl([v + 1 for v in levels], 50), "depth_max": max(levels) + 1 if levels else None}
     return lat, ok, closure
+
+
+def level_cap_leg(data, args, min_match, stream, local, ratio):
+    """The same data encoded with the dependency-level cap at 2 instead of 8:
+    its ratio, whole-file decode rate and random reads (the cap bounds the
+    wavefront depth of every read's closure at 3, at a ratio cost)."""
+    import torch
+
+    import paper_2606_18900_gb300 as ace
+
+    t = time.perf_counter()
+    arc_bytes = ace.encode(data, log2_B=args.log2_block, min_match=min_match, max_level=2,
+                           reads=ace.fastq_index(data))
+    enc_s = time.perf_counter() - t
+    with ace.Archive(arc_bytes, device=local) as arc:
+        out = torch.empty(data.size, dtype=torch.uint8, device=f"cuda:{local}")
+        run = lambda: arc.decode_all(out, stream)
+        for _ in range(args.warmup):
+            run()
+        arc.check(stream)
+        ok = bool(np.array_equal(out.cpu().numpy(), data))
+        step_ms = timed_steps(run, stream, args.steps)
+        arc.check(stream)
+        del out
+        lat, reads_ok, closure = (random_reads(arc, data, args.reads, 2, stream, f"cuda:{local}") if args.reads
+                                  else ([], True, None))
+    ms = float(np.mean(step_ms))
+    return {"what": "the workload's data encoded with the dependency-level cap 2 (the line's archive: cap 8)",
+            "ratio": round(data.size / arc_bytes.size, 3), "ratio_cap_8": round(ratio, 3),
+            "ms_per_step": ms, "gbs": data.size / (ms * 1e-3) / 1e9,
+            "random_read": {"p50_ms": pctl(lat, 50), "p99_ms": pctl(lat, 99), "n": len(lat), "closure": closure},
+            "encode_seconds": round(enc_s, 1), "bit_exact": ok and reads_ok}
 
 
 PHASES = ("cmd_rans", "parse", "lit_rans", "src_checks", "copies", "loop", "dep_waits")
@@ -358,7 +391,7 @@ def workload_fastq(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     size = args.size or (1 << 30)
     min_match = args.min_match or 16
-    data, arc_bytes, enc_s = make_fastq(size, args.log2_block, min_match, rank, world)
+    data, arc_bytes, enc_s = make_fastq(size, args.log2_block, min_match, rank, world, args.max_level)
     N = data.size
     arc = ace.Archive(arc_bytes, device=local)
     st = arc.stats()
@@ -409,6 +442,9 @@ def workload_fastq(args):
         serve = serve_compare(256_000_000, [100_000.0], 20_000, 4 << 30, 4, serial_n=300)
         serve["what"] = ("2,000-read FASTQ + 256 MB genome, 20,000 requests offered at 100k/s from the library's "
                          "submitting thread, against serial per-request decode")
+    level_cap = None
+    if rank == 0 and not args.no_side and args.max_level != 2:
+        level_cap = level_cap_leg(data, args, min_match, stream, local, ratio=N / arc_bytes.size)
 
     # end to end through the C ABI with host buffers, every step: the archive
     # from pinned host memory to the output in pinned host memory by one
@@ -458,19 +494,20 @@ def workload_fastq(args):
         config = {"workload": f"paired-end FASTQ {N} bytes, {1 << args.log2_block}-byte blocks, whole-file decode",
                   "log2_block": args.log2_block, "min_match": min_match, "ratio": round(N / arc_bytes.size, 3),
                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (archive and output > 126 MB)",
-                  "C_bytes": C, "U_bytes": U, "M_bytes": M, "max_level": st["max_level"],
+                  "C_bytes": C, "U_bytes": U, "M_bytes": M, "level_cap": args.max_level, "max_level": st["max_level"],
                   "level_histogram": arc.level_counts(), "encode_seconds": round(enc_s, 2)}
         line = base_line(
             args, value, total_ms / args.steps, world, config,
             roofline={"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                       "peak_kind": peak_kind, "kernel": "decode_kernel", "bytes_model": "C + U + M per launch",
                       "traffic": (recorded_traffic("fastq_1gib_log2B14")
-                                  if size == 1 << 30 and args.log2_block == 14 and min_match == 16 else None),
+                                  if size == 1 << 30 and args.log2_block == 14 and min_match == 16
+                                  and args.max_level == 8 else None),
                       "algorithmic_bytes": C + U + M},
             random_read={"p50_ms": pctl(lat, 50), "p99_ms": pctl(lat, 99), "n": len(lat),
                          "what": "read_lookup + aceapex_decode_range of one FASTQ record, synchronous",
                          "bit_exact": reads_ok, "closure": closure},
-            phase_split=phases, batch=batch, serve=serve,
+            phase_split=phases, batch=batch, serve=serve, level_cap_2=level_cap,
             cpu_baseline=cpu, e2e=e2e, gpu_launches=2 * args.steps, clocks=clk, bit_exact=ok,
             ms_median=float(np.median(step_ms)))
         print(json.dumps(line), flush=True)
