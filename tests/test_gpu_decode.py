@@ -284,6 +284,7 @@ def test_decode_host_one_call(window):
     with pytest.raises(ace.AceapexError) as e:
         ace.decode_host(bad, host)
     assert e.value.code == ace.ECORRUPT
+    ace.decode_host(ace.encode(np.zeros(0, np.uint8)), torch.zeros(0, dtype=torch.uint8))  # N = 0
 
 
 def test_level_counts_match_directory():
