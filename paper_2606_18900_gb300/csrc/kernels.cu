@@ -81,8 +81,16 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
 }
 
 // 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned)
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+// with an L2 cache policy
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint64_t pol) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "l"(pol) : "memory");
+}
+// L2 policy for data read once (the payload): evicted first, so that the
+// output, which matches read back, stays longer
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -320,9 +328,10 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
   // the payload is padded to 16 bytes, so no copy leaves the archive. wb is
   // the byte offset of the next word in the segment's word stream.
   const uint8_t *wsrc = pl + 128;
+  const uint64_t pol = policy_evict_first();
   auto fetch = [&](uint32_t blk) {
     const uint32_t wi = blk * 128 + (uint32_t)lane * 8;
-    if (lane < 16 && wi < nw) cp_async16(ring_s + (blk & 3) * 256 + lane * 16, wsrc + (size_t)wi * 2);
+    if (lane < 16 && wi < nw) cp_async16(ring_s + (blk & 3) * 256 + lane * 16, wsrc + (size_t)wi * 2, pol);
     cp_async_commit();
   };
   fetch(0);
