@@ -279,7 +279,7 @@ __device__ unsigned long long g_phase_cycles[16];
 // lut: the 4 x 4096-entry decode table (kSmemLut: at shared-window address
 // lut_s; otherwise global lut). st: the warp's command staging area. mt: the
 // warp's shared match table; ring_s: shared-window address of the warp's
-// 1 KiB renormalisation-word ring (1 KiB aligned).
+// 1,280-byte renormalisation-word ring (16-byte aligned).
 //
 // Phases: (1) rANS over the three command classes into the staging area;
 // (2) parse, scans and the checks of every command, rewriting each command's
@@ -323,15 +323,18 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
   if (!__all_sync(kFull, x >= kRansL)) ok = false;
   // Renormalisation words go through a 512-word ring in shared memory, filled
   // by cp.async in blocks of 128 words two blocks ahead of the reader, so the
-  // decode never waits on a global load between block boundaries. A lane
-  // copies a 16-byte chunk only if it starts before the segment's last word;
-  // the payload is padded to 16 bytes, so no copy leaves the archive. wb is
-  // the byte offset of the next word in the segment's word stream.
+  // decode never waits on a global load between block boundaries. Block slot
+  // 0 is also copied to the 256 bytes after the ring (lanes 16..31 make that
+  // copy), so the words of the next four steps are always contiguous from
+  // the read address wr: no step masks its address. A lane copies a 16-byte
+  // chunk only if it starts before the segment's last word; the payload is
+  // padded to 16 bytes, so no copy leaves the archive.
   const uint8_t *wsrc = pl + 128;
   const uint64_t pol = policy_evict_first();
   auto fetch = [&](uint32_t blk) {
-    const uint32_t wi = blk * 128 + (uint32_t)lane * 8;
-    if (lane < 16 && wi < nw) cp_async16(ring_s + (blk & 3) * 256 + lane * 16, wsrc + (size_t)wi * 2, pol);
+    const uint32_t wi = blk * 128 + (uint32_t)(lane & 15) * 8;
+    const uint32_t to = ring_s + (lane < 16 ? (blk & 3) * 256 : 1024u) + (lane & 15) * 16;
+    if ((lane < 16 || (blk & 3) == 0) && wi < nw) cp_async16(to, wsrc + (size_t)wi * 2, pol);
     cp_async_commit();
   };
   fetch(0);
@@ -340,12 +343,20 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
   fetch(3);
   cp_async_wait<2>();
   __syncwarp();
-  uint32_t blk = 0, wb = 0;
+  // blk: the block being read; wr: shared address of the next word; bnd: end
+  // of blk's slot (wr moves on into the next slot, or into the copy of slot
+  // 0, which it leaves for slot 0 itself when blk advances)
+  uint32_t blk = 0, wr = ring_s, bnd = ring_s + 256;
   const uint32_t lt = lanemask_lt();
   // after the step that consumed the last word of a block: reuse its slot
   auto advance = [&]() {
-    if ((wb >> 8) != blk) {
-      blk = wb >> 8;
+    if (wr >= bnd) {
+      ++blk;
+      bnd += 256;
+      if (bnd > ring_s + 1024) {
+        wr -= 1024;
+        bnd -= 1024;
+      }
       __syncwarp();
       fetch(blk + 3);
       cp_async_wait<2>();
@@ -361,9 +372,9 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
   // order (every lane reads a ring word; only those lanes use it)
   auto renorm = [&](bool need) {
     const uint32_t m = __ballot_sync(kFull, need);
-    const uint32_t w = lds_u16(((wb + 2 * __popc(m & lt)) & 1023u) | ring_s);
+    const uint32_t w = lds_u16(wr + 2 * __popc(m & lt));
     if (need) x = __byte_perm(w, x, 0x5410);  // x << 16 | w
-    wb += 2 * __popc(m);
+    wr += 2 * __popc(m);
   };
   // one interleaved step of the command classes: lane j decodes symbol q
   auto cmd_step = [&](uint32_t q) -> uint32_t {
@@ -396,7 +407,7 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
   // (1) command classes; the step that crosses into the literals keeps its
   // literal symbol in `pend` until the command prefixes exist. Four steps take
   // at most 128 words, so after an advance() (blocks blk and blk + 1 complete,
-  // wb inside blk) four steps read only those two blocks.
+  // wr inside blk's slot) four steps read only those two blocks.
   uint32_t t0 = 0, pend = 0;
   if (ok) {
     // four steps inside one class: the table row is known for all lanes
@@ -537,6 +548,9 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
       t0 += 32;
     }
   }
+  // words consumed: the blocks before the current ring cycle plus the offset
+  // of wr in the ring (and its copy of slot 0)
+  const uint32_t wb = (blk & ~3u) * 256 + (wr - ring_s);
   if (!__all_sync(kFull, x == kRansL) || wb != 2 * nw) ok = false;
   __syncwarp();
   PHASE_MARK(2);
@@ -590,7 +604,8 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
     }
     // (the hazard ranges need no flag: they are found while the loads above
     // are in flight, and the loaded values are used only after them)
-    mt->src[lane] = src;
+    // linear view: the table holds each match's source address
+    mt->src[lane] = kMode == kViewLinear ? (uint64_t)reinterpret_cast<uintptr_t>(V.base + (src - V.origin)) : src;
     mt->dst[lane] = dst;
     __syncwarp();
     // The earlier matches of this chunk whose outputs overlap this match's
@@ -606,16 +621,19 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
       const uint32_t s_rel = valid && src > seg_start ? (uint32_t)(src - seg_start) : 0u;
       const uint32_t d_off = valid ? (uint32_t)(dst - seg_start) : 0xFFFFFFFFu;
       const uint32_t d_end = valid ? d_off + ml : 0xFFFFFFFFu;
-      uint32_t jh = 0, jl = 0;
+      // (no search when every source ends before the chunk's first output)
+      if (__any_sync(kFull, se_rel > __shfl_sync(kFull, d_off, 0))) {
+        uint32_t jh = 0, jl = 0;
 #pragma unroll
-      for (int s = 16; s; s >>= 1) {
-        if (__shfl_sync(kFull, d_off, jh + s) < se_rel) jh += s;
-        if (__shfl_sync(kFull, d_end, jl + s) <= s_rel) jl += s;
+        for (int s = 16; s; s >>= 1) {
+          if (__shfl_sync(kFull, d_off, jh + s) < se_rel) jh += s;
+          if (__shfl_sync(kFull, d_end, jl + s) <= s_rel) jl += s;
+        }
+        const bool any_h = __shfl_sync(kFull, d_off, jh) < se_rel;  // some output starts before the source ends
+        const bool any_l = __shfl_sync(kFull, d_end, jl) <= s_rel;  // some output ends before the source starts
+        const uint32_t jlo = any_l ? jl + 1 : 0;
+        if (any_h && jlo <= jh) hmask = ((2u << jh) - 1u) & ~((1u << jlo) - 1u);
       }
-      const bool any_h = __shfl_sync(kFull, d_off, jh) < se_rel;  // some output starts before the source ends
-      const bool any_l = __shfl_sync(kFull, d_end, jl) <= s_rel;  // some output ends before the source starts
-      const uint32_t jlo = any_l ? jl + 1 : 0;
-      if (any_h && jlo <= jh) hmask = ((2u << jh) - 1u) & ~((1u << jlo) - 1u);
     }
     if (__any_sync(kFull, bad)) {
       ok = false;
@@ -667,18 +685,32 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
           const uint32_t b16 = (doff & ~15u) + ((uu - mt->start[m]) << 4);
           const uint32_t a0 = max(doff, b16), a1 = min(doff + mt->len[m], b16 + 16);
           const uint32_t o = a0 - b16, n = a1 - a0;
-          const uint64_t P = mt->src[m] + (a0 - doff);
-          const uint8_t *pa = src_at<kMode>(V, P, log2_S);
-          const uint32_t dl = (uint32_t)reinterpret_cast<uintptr_t>(pa) & 15u;
           uint4 X = make_uint4(0, 0, 0, 0), Y = X;
           uint32_t cc;
-          if (dl >= o) {
-            X = *reinterpret_cast<const uint4 *>(pa - dl);
-            if (dl + n > 16) Y = *reinterpret_cast<const uint4 *>(src_at<kMode>(V, P + (16 - dl), log2_S));
-            cc = dl - o;
+          if (kMode == kViewLinear) {
+            const uint8_t *pa = reinterpret_cast<const uint8_t *>(mt->src[m] + (a0 - doff));
+            const uint32_t dl = (uint32_t)reinterpret_cast<uintptr_t>(pa) & 15u;
+            const uint4 *pb = reinterpret_cast<const uint4 *>(pa - dl);
+            if (dl >= o) {
+              X = pb[0];
+              if (dl + n > 16) Y = pb[1];
+              cc = dl - o;
+            } else {
+              Y = pb[0];
+              cc = 16 + dl - o;
+            }
           } else {
-            Y = *reinterpret_cast<const uint4 *>(pa - dl);
-            cc = 16 + dl - o;
+            const uint64_t P = mt->src[m] + (a0 - doff);
+            const uint8_t *pa = src_at<kMode>(V, P, log2_S);
+            const uint32_t dl = (uint32_t)reinterpret_cast<uintptr_t>(pa) & 15u;
+            if (dl >= o) {
+              X = *reinterpret_cast<const uint4 *>(pa - dl);
+              if (dl + n > 16) Y = *reinterpret_cast<const uint4 *>(src_at<kMode>(V, P + (16 - dl), log2_S));
+              cc = dl - o;
+            } else {
+              Y = *reinterpret_cast<const uint4 *>(pa - dl);
+              cc = 16 + dl - o;
+            }
           }
           // cc < 16 in both cases (dl, o < 16): the mask tells the compiler,
           // which drops the selection level that a shift of 16 or more needs
@@ -689,22 +721,44 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
             *reinterpret_cast<uint4 *>(to) = make_uint4(r[0], r[1], r[2], r[3]);
           } else {
             // bytes [o, o + n) of the block as naturally aligned pieces of
-            // 1, 2, 4 and 8 bytes, rising in size up to the first boundary
-            // that the next piece would cross, then falling: at most eight
-            // store instructions per warp for any mix of partial blocks (a
-            // scattered store costs the memory pipeline one pass per line
-            // it touches, whatever its width)
+            // 1, 2, 4 and 8 bytes (a scattered store costs the memory
+            // pipeline one pass per line it touches, whatever its width)
             auto wd = [&](uint32_t i) { return i & 2 ? (i & 1 ? r[3] : r[2]) : (i & 1 ? r[1] : r[0]); };
-            uint32_t a = o;
-            const uint32_t e = o + n;
-            if ((a & 1) && a < e) { to[a] = (uint8_t)(wd(a >> 2) >> (8 * (a & 3))); a += 1; }
-            if ((a & 2) && a + 2 <= e) { *reinterpret_cast<uint16_t *>(to + a) = (uint16_t)(wd(a >> 2) >> (8 * (a & 2))); a += 2; }
-            if ((a & 4) && a + 4 <= e) { *reinterpret_cast<uint32_t *>(to + a) = wd(a >> 2); a += 4; }
-            if ((a & 8) && a + 8 <= e) { *reinterpret_cast<uint2 *>(to + a) = make_uint2(r[2], r[3]); a += 8; }
-            if (a + 8 <= e) { *reinterpret_cast<uint2 *>(to + a) = (a & 8) ? make_uint2(r[2], r[3]) : make_uint2(r[0], r[1]); a += 8; }
-            if (a + 4 <= e) { *reinterpret_cast<uint32_t *>(to + a) = wd(a >> 2); a += 4; }
-            if (a + 2 <= e) { *reinterpret_cast<uint16_t *>(to + a) = (uint16_t)(wd(a >> 2) >> (8 * (a & 2))); a += 2; }
-            if (a < e) to[a] = (uint8_t)(wd(a >> 2) >> (8 * (a & 3)));
+            if (o == 0 || o + n == 16) {
+              // the first or last block of a match: one end of the bytes is
+              // an end of the block, and the pieces are the set bits of n,
+              // rising in size from o when the bytes end at the block's end,
+              // falling from 0 when they start at its start (four store
+              // instructions per warp)
+              const bool rise = o != 0;
+              if (n & 8) *reinterpret_cast<uint2 *>(to + (rise ? 8 : 0)) = rise ? make_uint2(r[2], r[3]) : make_uint2(r[0], r[1]);
+              if (n & 4) {
+                const uint32_t a = rise ? o + (n & 3) : (n & 8);
+                *reinterpret_cast<uint32_t *>(to + a) = wd(a >> 2);
+              }
+              if (n & 2) {
+                const uint32_t a = rise ? o + (n & 1) : (n & 12);
+                *reinterpret_cast<uint16_t *>(to + a) = (uint16_t)(wd(a >> 2) >> (8 * (a & 2)));
+              }
+              if (n & 1) {
+                const uint32_t a = rise ? o : (n & 14);
+                to[a] = (uint8_t)(wd(a >> 2) >> (8 * (a & 3)));
+              }
+            } else {
+              // both ends inside the block (a match shorter than 16 bytes):
+              // rising in size up to the first boundary that the next piece
+              // would cross, then falling (eight store instructions)
+              uint32_t a = o;
+              const uint32_t e = o + n;
+              if ((a & 1) && a < e) { to[a] = (uint8_t)(wd(a >> 2) >> (8 * (a & 3))); a += 1; }
+              if ((a & 2) && a + 2 <= e) { *reinterpret_cast<uint16_t *>(to + a) = (uint16_t)(wd(a >> 2) >> (8 * (a & 2))); a += 2; }
+              if ((a & 4) && a + 4 <= e) { *reinterpret_cast<uint32_t *>(to + a) = wd(a >> 2); a += 4; }
+              if ((a & 8) && a + 8 <= e) { *reinterpret_cast<uint2 *>(to + a) = make_uint2(r[2], r[3]); a += 8; }
+              if (a + 8 <= e) { *reinterpret_cast<uint2 *>(to + a) = (a & 8) ? make_uint2(r[2], r[3]) : make_uint2(r[0], r[1]); a += 8; }
+              if (a + 4 <= e) { *reinterpret_cast<uint32_t *>(to + a) = wd(a >> 2); a += 4; }
+              if (a + 2 <= e) { *reinterpret_cast<uint16_t *>(to + a) = (uint16_t)(wd(a >> 2) >> (8 * (a & 2))); a += 2; }
+              if (a < e) to[a] = (uint8_t)(wd(a >> 2) >> (8 * (a & 3)));
+            }
           }
         } else {
           const uint32_t o = (uu - mt->start[m]) << 4;
@@ -712,6 +766,11 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
           const uint64_t pp = mt->src[m] + o;
           uint8_t *to = out + (mt->dst[m] - seg_start) + o;
           uint8_t v[16];
+          if (kMode == kViewLinear) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if ((uint32_t)j < n) v[j] = reinterpret_cast<const uint8_t *>(pp)[j];
+          } else
 #pragma unroll
           for (int j = 0; j < 16; ++j)
             if ((uint32_t)j < n) v[j] = *src_at<kMode>(V, pp + j, log2_S);
@@ -752,9 +811,9 @@ __device__ __forceinline__ void decode_segment(const DecodeLaunch &L, const DevA
                                                      mt, smem_addr(ring), lane, d, ph, ph_t);
 }
 
-// Dynamic shared memory of a decode CTA: the decode table (64 KiB), then,
-// from the next 1 KiB boundary, a 1 KiB word ring per warp, then a match table
-// and a command stage per warp.
+// Dynamic shared memory of a decode CTA: the decode table (64 KiB), then a
+// 1,280-byte word ring per warp (the 1 KiB ring and a copy of its first 256
+// bytes), then a match table and a command stage per warp.
 struct WarpSmem {
   uint32_t *lut;
   uint16_t *ring;
@@ -765,11 +824,10 @@ __device__ __forceinline__ WarpSmem warp_smem(uint8_t *smem, int wid) {
   constexpr uint32_t nw = kDecodeThreads / 32;
   WarpSmem w;
   w.lut = reinterpret_cast<uint32_t *>(smem);
-  const uint32_t base = smem_addr(smem) + kLutBytes;
-  uint8_t *rings = smem + kLutBytes + (((base + 1023u) & ~1023u) - base);
-  w.ring = reinterpret_cast<uint16_t *>(rings) + wid * 512;
-  w.mt = reinterpret_cast<MatchTable *>(rings + nw * 1024) + wid;
-  w.stage = rings + nw * (1024 + sizeof(MatchTable)) + (size_t)wid * kSmemStage;
+  uint8_t *rings = smem + kLutBytes;
+  w.ring = reinterpret_cast<uint16_t *>(rings + wid * 1280);
+  w.mt = reinterpret_cast<MatchTable *>(rings + nw * 1280) + wid;
+  w.stage = rings + nw * (1280 + sizeof(MatchTable)) + (size_t)wid * kSmemStage;
   return w;
 }
 
@@ -1250,10 +1308,9 @@ __global__ void interleave_kernel(LineStreams S, uint8_t *out) {
 
 // ------------------------------------------------------------------ launchers
 
-constexpr size_t kWarpSmem = sizeof(MatchTable) + 1024 + kSmemStage;
+constexpr size_t kWarpSmem = sizeof(MatchTable) + 1280 + kSmemStage;
 static_assert(sizeof(MatchTable) % 16 == 0, "keeps the stages aligned");
-// + 1 KiB: the rings start at the first 1 KiB boundary after the table
-constexpr size_t kSmemLutBytes = kLutBytes + 1024 + (size_t)(kDecodeThreads / 32) * kWarpSmem;
+constexpr size_t kSmemLutBytes = kLutBytes + (size_t)(kDecodeThreads / 32) * kWarpSmem;
 
 int decode_grid(int device, int block) {
   (void)block;
@@ -1540,9 +1597,8 @@ __global__ void __launch_bounds__(256) noalloc_decode_kernel(DecodeLaunch L, uin
   uint8_t *stage = g_noalloc_scratch + kNoAllocCtlBytes + kNoAllocLutBytes + kNoAllocFlagBytes +
                    (size_t)gwarp * kStageBytes;
   __shared__ MatchTable mts[8];
-  __shared__ __align__(16) uint16_t rings_raw[9][512];  // eight 1 KiB rings from the first 1 KiB boundary
-  const uint32_t rb = smem_addr(rings_raw);
-  uint16_t *ring = &rings_raw[0][0] + ((((rb + 1023u) & ~1023u) - rb) >> 1) + (threadIdx.x >> 5) * 512;
+  __shared__ __align__(16) uint16_t rings_raw[8][640];
+  uint16_t *ring = rings_raw[threadIdx.x >> 5];
   const uint32_t epoch = ld_relaxed(L.epoch);
   PHASE_DECL;
   const uint32_t empty = reinterpret_cast<const uint32_t *>(g_noalloc_scratch)[kCtlEmpty / 4];
