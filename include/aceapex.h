@@ -234,7 +234,7 @@ int aceapex_decode_batch(aceapex_archive *const *as, int n, void *const *d_outs,
  * aceapex_server_create: serve the n archives as[0..n) (same device; the
  * server does not own them and they must outlive it; do not call other
  * decode functions on them while the server runs). mem_budget: device bytes
- * for the server (per-slot page tables and flags, 8 bytes per segment per
+ * for the server (per-slot page tables and flags, 12 bytes per segment per
  * slot, and the decode arenas, the rest split evenly over the slots). slots:
  * batches that may be in flight at once (1..64), each on its own stream. A
  * worker thread forms batches from the queue in arrival order while the union
@@ -300,7 +300,7 @@ int aceapex_server_get_stats(aceapex_server *s, aceapex_server_stats *out);
  * queued on `stream` has run. The header (128 bytes) is read to the host
  * first, so the call synchronises `stream` once before queuing the decode.
  *
- * Scratch: a fixed array of about 4.3 MiB in the library's device memory,
+ * Scratch: a fixed array of about 4.6 MiB in the library's device memory,
  * which every GPU that loads the library holds until the process exits. The
  * first call on a device looks up the array's device address (with that
  * device current). Archives

@@ -128,7 +128,7 @@ struct aceapex_archive {
   DBuf<uint8_t> d_payload;
   DBuf<SegRec> d_dir;
   DBuf<uint32_t> d_lut;
-  DBuf<uint32_t> d_flags;
+  DBuf<uint64_t> d_flags;   // level << 32 | epoch of the call that completed the segment
   DBuf<WorkItem> d_order;    // all segments in level order
   DBuf<uint32_t> d_words;    // [0] err, [1] epoch, [2] counter
   DBuf<uint8_t> d_blocked;

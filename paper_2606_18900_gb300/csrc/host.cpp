@@ -611,7 +611,12 @@ int open_archive(const void *h_archive, uint64_t nbytes, int device, aceapex_arc
   if (e == cudaSuccess) e = cudaMemcpy(A->d_lut.p, lut.data(), 4 * lut.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && h.n_seg)
     e = cudaMemcpy(A->d_order.p, order.data(), sizeof(WorkItem) * h.n_seg, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(A->d_flags.p, 0, 4 * std::max<uint64_t>(h.n_seg, 1));
+  if (e == cudaSuccess) {
+    // each segment's flag word starts with its level and no epoch
+    std::vector<uint64_t> f(std::max<uint64_t>(h.n_seg, 1), 0);
+    for (uint64_t s = 0; s < h.n_seg; ++s) f[s] = (uint64_t)A->dir[s].level << 32;
+    e = cudaMemcpy(A->d_flags.p, f.data(), 8 * f.size(), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMemset(A->d_words.p, 0, 16);
   if (e == cudaSuccess) e = cudaMemset(A->d_blocked.p, 0, std::max<uint64_t>(h.n_seg, 1));
   if (e != cudaSuccess) {

@@ -36,14 +36,14 @@ namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
-__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_release(uint64_t *p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
@@ -111,10 +111,10 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
 // Wait until every lane with `need` sees *flag == epoch. False on timeout or
 // when another warp has latched an error. Lane 0 reads the error word and
 // the clock and decides for the warp (see take_item).
-__device__ bool wait_flags(const uint32_t *flag, bool need, uint32_t epoch, uint64_t deadline, uint32_t *err,
+__device__ bool wait_flags(const uint64_t *flag, bool need, uint32_t epoch, uint64_t deadline, uint32_t *err,
                            int lane) {
   for (uint32_t spin = 0;; ++spin) {
-    bool ok = !need || ld_acquire(flag) == epoch;
+    bool ok = !need || (uint32_t)ld_acquire(flag) == epoch;
     if (__all_sync(kFull, ok)) return true;
     uint32_t why = 0;
     if (lane == 0) why = ld_relaxed(err) != 0 ? 1u : now_ns() > deadline ? 2u : 0u;
@@ -588,19 +588,21 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
     const bool need0 = valid && q0 != seg;
     const bool need1 = valid && q1 != q0 && q1 != seg;
     // A source segment must have a lower level than ours (a wait on any other
-    // could not end) and, in a paged view, be present. Its flag is read in
-    // the same pass.
+    // could not end) and, in a paged view, be present. Its level is the high
+    // half of its flag word, read in the same load as its epoch.
     bool bad = false;
     uint32_t f0 = epoch, f1 = epoch;
     if (need0) {
-      bad |= A.dir[q0].level >= my_level;
+      const uint64_t f = ld_acquire(A.flags + q0);
+      bad |= (uint32_t)(f >> 32) >= my_level;
       if (kMode == kViewPaged) bad |= V.page[q0] == 0xFFFFFFFFu;
-      f0 = ld_acquire(A.flags + q0);
+      f0 = (uint32_t)f;
     }
     if (need1) {
-      bad |= A.dir[q1].level >= my_level;
+      const uint64_t f = ld_acquire(A.flags + q1);
+      bad |= (uint32_t)(f >> 32) >= my_level;
       if (kMode == kViewPaged) bad |= V.page[q1] == 0xFFFFFFFFu;
-      f1 = ld_acquire(A.flags + q1);
+      f1 = (uint32_t)f;
     }
     // (the hazard ranges need no flag: they are found while the loads above
     // are in flight, and the loaded values are used only after them)
@@ -790,7 +792,7 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
   // ------------------------------------------------------------- publish
   __threadfence();
   __syncwarp();
-  if (lane == 0 && ok && !(A.blocked && A.blocked[seg])) st_release(A.flags + seg, epoch);
+  if (lane == 0 && ok && !(A.blocked && A.blocked[seg])) st_release(A.flags + seg, (uint64_t)d.level << 32 | epoch);
 }
 
 // Decode one segment: its command streams are staged in the warp's shared
@@ -1541,7 +1543,7 @@ constexpr uint32_t kNoAllocMaxSegments = 65536;
 constexpr uint32_t kNoAllocWarps = 256;
 constexpr size_t kNoAllocCtlBytes = 256;                       // counter, epoch, err
 constexpr size_t kNoAllocLutBytes = 4 * kScale * sizeof(uint32_t);
-constexpr size_t kNoAllocFlagBytes = kNoAllocMaxSegments * sizeof(uint32_t);
+constexpr size_t kNoAllocFlagBytes = kNoAllocMaxSegments * sizeof(uint64_t);
 constexpr size_t kNoAllocStageBytes = (size_t)kNoAllocWarps * kStageBytes;
 constexpr size_t kNoAllocBytes = kNoAllocCtlBytes + kNoAllocLutBytes + kNoAllocFlagBytes + kNoAllocStageBytes;
 
@@ -1585,6 +1587,16 @@ __global__ void noalloc_setup_kernel(const uint8_t *tables) {
     ctl[kCtlEmpty / 4] = empty;
     ctl[kCtlEpoch / 4] = ctl[kCtlEpoch / 4] + 1u;
   }
+}
+
+// each segment's flag word: its directory level, no epoch (the level of a
+// corrupt record is caught by that segment's own checks, and a reader that
+// waits for it gives up once that segment latches the error)
+__global__ void noalloc_levels_kernel(const SegRec *dir, uint32_t n_seg) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n_seg)
+    reinterpret_cast<uint64_t *>(g_noalloc_scratch + kNoAllocCtlBytes + kNoAllocLutBytes)[s] = (uint64_t)dir[s].level
+                                                                                                << 32;
 }
 
 // segments in index order (every source segment precedes its reader, so a
@@ -1690,7 +1702,7 @@ extern "C" int aceapex_decode_all_noalloc(const void *d_archive, uint64_t nbytes
   A.payload = arc + off_payload;
   A.dir = reinterpret_cast<const SegRec *>(arc + off_dir);
   A.lut = reinterpret_cast<const uint32_t *>(base + kNoAllocCtlBytes);
-  A.flags = reinterpret_cast<uint32_t *>(base + kNoAllocCtlBytes + kNoAllocLutBytes);
+  A.flags = reinterpret_cast<uint64_t *>(base + kNoAllocCtlBytes + kNoAllocLutBytes);
   A.blocked = nullptr;
   A.n = n;
   A.D = u64(32);
@@ -1708,6 +1720,7 @@ extern "C" int aceapex_decode_all_noalloc(const void *d_archive, uint64_t nbytes
   L.scratch_warps = kNoAllocWarps;
   L.wait_ns = 2000000000ull;
   noalloc_setup_kernel<<<1, 256, 0, st>>>(arc + kHeaderBytes);
+  noalloc_levels_kernel<<<(unsigned)((n_seg + 255) / 256), 256, 0, st>>>(A.dir, (uint32_t)n_seg);
   noalloc_decode_kernel<<<kNoAllocWarps / 8, 256, 0, st>>>(L, payload_bytes, h[30]);
   noalloc_status_kernel<<<1, 1, 0, st>>>(d_status);
   return cudaGetLastError() == cudaSuccess ? 0 : 4;

@@ -24,7 +24,7 @@ struct DevArchive {
   const SegRec *dir;        // segment directory
   const WorkItem *order;    // all segments in level order
   const uint32_t *lut;      // 4 classes x 4096 slots: sym | bias << 8 | (freq - 1) << 20
-  uint32_t *flags;          // per-segment ready flag (= epoch when complete)
+  uint64_t *flags;          // per segment: its level << 32 | the epoch of the call that completed it
   const uint8_t *blocked;   // test hook: per-segment "never publish" bytes, or nullptr
   uint64_t n;               // decompressed size
   uint64_t D;               // distance bound (0 = none)

@@ -49,7 +49,8 @@ struct Req {
 struct Slot {
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;
-  std::vector<DBuf<uint32_t>> page, flags;  // per archive
+  std::vector<DBuf<uint32_t>> page;  // per archive
+  std::vector<DBuf<uint64_t>> flags;
   DBuf<uint8_t> arena;
   DBuf<WorkItem> work;
   DBuf<GatherJob> jobs;
@@ -296,10 +297,10 @@ int aceapex_server_create(aceapex_archive *const *as, int n, uint64_t mem_budget
     delete S;
     return ACEAPEX_ECUDA;
   }
-  // page tables and flags (8 bytes per segment per slot) come out of the budget
+  // page tables and flags (12 bytes per segment per slot) come out of the budget
   uint64_t fixed = 0, need_stage = 0, seg_bytes = 0;
   for (aceapex_archive *A : S->arcs) {
-    fixed += 8 * A->h.n_seg * (uint64_t)slots;
+    fixed += 12 * A->h.n_seg * (uint64_t)slots;
     seg_bytes = std::max<uint64_t>(seg_bytes, uint64_t(1) << A->h.log2_S);
     int rc = ensure_scratch(A, 0);
     if (rc) {
@@ -330,8 +331,11 @@ int aceapex_server_create(aceapex_archive *const *as, int n, uint64_t mem_budget
     slot.flags.resize(n);
     for (int i = 0; ok && i < n; ++i) {
       const uint64_t ns = std::max<uint64_t>(S->arcs[i]->h.n_seg, 1);
+      // (the flag words start as the archive's: the levels, and epochs of
+      // earlier calls, which no later call matches)
       ok = slot.page[i].alloc(ns) == cudaSuccess && slot.flags[i].alloc(ns) == cudaSuccess &&
-           cudaMemset(slot.page[i].p, 0xFF, 4 * ns) == cudaSuccess && cudaMemset(slot.flags[i].p, 0, 4 * ns) == cudaSuccess;
+           cudaMemset(slot.page[i].p, 0xFF, 4 * ns) == cudaSuccess &&
+           cudaMemcpy(slot.flags[i].p, S->arcs[i]->d_flags.p, 8 * ns, cudaMemcpyDeviceToDevice) == cudaSuccess;
     }
     if (!ok) {
       aceapex_server_destroy(S);

@@ -116,7 +116,8 @@ def test_admission_refusal_and_queueing(corpus):
     fq, fa, a_fq, a_fa = corpus
     # arenas of 48 segments: a 2 MiB range (128 segments) can never fit; a read
     # of the 42-segment FASTQ always can
-    budget = 8 * (a_fq.stats()["n_segments"] + a_fa.stats()["n_segments"]) * 2 + 2 * 48 * 16384
+    # (per slot and segment: a 4-byte page-table entry and an 8-byte flag word)
+    budget = 12 * (a_fq.stats()["n_segments"] + a_fa.stats()["n_segments"]) * 2 + 2 * 48 * 16384
     with ace.Server([a_fq, a_fa], mem_budget=budget, slots=2) as srv:
         big = torch.zeros(2 << 20, dtype=torch.uint8, device="cuda")
         with pytest.raises(ace.AceapexError) as e:
