@@ -17,8 +17,10 @@
 //      output position.
 //   4. bounded waits on the ready flags of source segments, then match copies
 //      in hazard-free rounds spread over the lanes.
-//   5. publish: every lane fences, then lane 0 stores the epoch into the
-//      segment's flag with release semantics.
+//   5. publish: the warp synchronises (which orders every lane's output
+//      stores before what lane 0 does next), then lane 0 stores the level and
+//      epoch into the segment's flag with release semantics, a release that
+//      covers the other lanes' stores through that ordering.
 // Errors latch the first code into a device word; waits give up at a time
 // limit (globaltimer) or as soon as another warp has latched an error.
 #include <cuda_runtime.h>
@@ -790,7 +792,8 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
 
   PHASE_COUNT(9, 1);
   // ------------------------------------------------------------- publish
-  __threadfence();
+  // (no fence per lane: the warp barrier orders every lane's stores before
+  // lane 0's release store, and release is cumulative)
   __syncwarp();
   if (lane == 0 && ok && !(A.blocked && A.blocked[seg])) st_release(A.flags + seg, (uint64_t)d.level << 32 | epoch);
 }
