@@ -549,11 +549,18 @@ constexpr uint64_t kUploadPiece = uint64_t(32) << 20;
 // all that precedes the first copy back, so windows are kept short.
 constexpr uint64_t kHostWindow = uint64_t(64) << 20;
 
+int upload_pieces(aceapex_archive *A, const uint8_t *src, uint64_t bytes, uint64_t limit);
+
+// Payload bytes a one-call decode uploads before its host checks: what the
+// first windows read, so that their decodes need not wait for the rest
+constexpr uint64_t kEarlyUpload = 2 * kUploadPiece;
+
 // aceapex_open. With defer_payload (aceapex_decode_host) the host checks
 // leave out the dependency lists and the read index, which a whole-file
-// decode does not read, and the payload is not copied: start_payload_upload
-// copies it afterwards, once the small sections are on the device, so that
-// their copies do not queue behind it.
+// decode does not read, no whole-file work list is made (the windows have
+// their own), and only the payload's first pieces are copied while the host
+// checks run: start_payload_upload copies the rest afterwards, once the small
+// sections are on their way, so that their copies do not queue behind it.
 int open_archive(const void *h_archive, uint64_t nbytes, int device, aceapex_archive **out, bool defer_payload) {
   if (!h_archive || !out || nbytes == 0) return ACEAPEX_EINVAL;
   *out = nullptr;
@@ -578,6 +585,10 @@ int open_archive(const void *h_archive, uint64_t nbytes, int device, aceapex_arc
       A->d_payload.alloc(pay_bytes) == cudaSuccess &&
       cudaMemcpyAsync(A->d_payload.p, a + pay_off, pay_bytes, cudaMemcpyHostToDevice, up) == cudaSuccess)
     uploading = true;
+  bool early = false;
+  if (defer_payload && dev_ok && pay_bytes && A->d_payload.alloc(pay_bytes) == cudaSuccess &&
+      upload_pieces(A, a + pay_off, pay_bytes, kEarlyUpload) == ACEAPEX_OK)
+    early = true;
   int rc = validate(a, nbytes, A, !defer_payload);
   const bool upload_ok = !uploading || cudaStreamSynchronize(up) == cudaSuccess;
   if (up) cudaStreamDestroy(up);
@@ -589,15 +600,16 @@ int open_archive(const void *h_archive, uint64_t nbytes, int device, aceapex_arc
   std::vector<uint32_t> lut;
   build_lut(a, lut);
   std::vector<WorkItem> order;
-  level_order(A->dir, nullptr, A->h.n_seg, 0, order);
+  if (!defer_payload) level_order(A->dir, nullptr, A->h.n_seg, 0, order);
   const Header &h = A->h;
   // (the payload buffer is the uploaded one when the header's payload fields
   // were what validation accepted, else it is allocated and copied now)
-  const bool have_payload = uploading && pay_off == h.off_payload && pay_bytes == h.payload_bytes;
+  const bool have_payload = (uploading || early) && pay_off == h.off_payload && pay_bytes == h.payload_bytes;
   bool okm = (have_payload || A->d_payload.alloc(std::max<uint64_t>(h.payload_bytes, 16)) == cudaSuccess) &&
              A->d_dir.alloc(std::max<uint64_t>(h.n_seg, 1)) == cudaSuccess &&
              A->d_lut.alloc(4 * kScale) == cudaSuccess && A->d_flags.alloc(std::max<uint64_t>(h.n_seg, 1)) == cudaSuccess &&
-             A->d_order.alloc(std::max<uint64_t>(h.n_seg, 1)) == cudaSuccess && A->d_words.alloc(4) == cudaSuccess &&
+             (defer_payload || A->d_order.alloc(std::max<uint64_t>(h.n_seg, 1)) == cudaSuccess) &&
+             A->d_words.alloc(4) == cudaSuccess &&
              A->d_blocked.alloc(std::max<uint64_t>(h.n_seg, 1)) == cudaSuccess;
   if (!okm || !global_epoch(device)) {
     A->release();
@@ -609,16 +621,16 @@ int open_archive(const void *h_archive, uint64_t nbytes, int device, aceapex_arc
     e = cudaMemcpy(A->d_payload.p, a + h.off_payload, h.payload_bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && h.n_seg) e = cudaMemcpy(A->d_dir.p, A->dir.data(), 24 * h.n_seg, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(A->d_lut.p, lut.data(), 4 * lut.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && h.n_seg)
+  if (e == cudaSuccess && h.n_seg && !defer_payload)
     e = cudaMemcpy(A->d_order.p, order.data(), sizeof(WorkItem) * h.n_seg, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) {
-    // each segment's flag word starts with its level and no epoch
-    std::vector<uint64_t> f(std::max<uint64_t>(h.n_seg, 1), 0);
-    for (uint64_t s = 0; s < h.n_seg; ++s) f[s] = (uint64_t)A->dir[s].level << 32;
-    e = cudaMemcpy(A->d_flags.p, f.data(), 8 * f.size(), cudaMemcpyHostToDevice);
-  }
+  // each segment's flag word starts with its level and no epoch (made on the
+  // device from the directory copied above, on the legacy stream, which
+  // orders it before the synchronous copies below)
+  if (e == cudaSuccess) e = launch_init_flags(A->d_flags.p, A->d_dir.p, h.n_seg, 0);
   if (e == cudaSuccess) e = cudaMemset(A->d_words.p, 0, 16);
   if (e == cudaSuccess) e = cudaMemset(A->d_blocked.p, 0, std::max<uint64_t>(h.n_seg, 1));
+  // (the caller's streams need not synchronise with the legacy stream)
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
   if (e != cudaSuccess) {
     A->release();
     delete A;
@@ -628,15 +640,15 @@ int open_archive(const void *h_archive, uint64_t nbytes, int device, aceapex_arc
   return ACEAPEX_OK;
 }
 
-// The payload of a handle opened with defer_payload, in pieces on the
-// handle's upload stream, each followed by an event (up_ev / up_end).
-int start_payload_upload(aceapex_archive *A, const void *h_archive) {
-  const Header &h = A->h;
-  if (!h.payload_bytes) return ACEAPEX_OK;
-  if (cudaStreamCreateWithFlags(&A->up_st, cudaStreamNonBlocking) != cudaSuccess) return ACEAPEX_ECUDA;
-  const uint8_t *src = static_cast<const uint8_t *>(h_archive) + h.off_payload;
-  for (uint64_t o = 0; o < h.payload_bytes; o += kUploadPiece) {
-    const uint64_t n = std::min(kUploadPiece, h.payload_bytes - o);
+// Payload bytes [issued, min(limit, bytes)) of a handle opened with
+// defer_payload, in pieces on the handle's upload stream, each followed by an
+// event (up_ev / up_end); src is the payload in host memory.
+int upload_pieces(aceapex_archive *A, const uint8_t *src, uint64_t bytes, uint64_t limit) {
+  if (!bytes) return ACEAPEX_OK;
+  if (!A->up_st && cudaStreamCreateWithFlags(&A->up_st, cudaStreamNonBlocking) != cudaSuccess) return ACEAPEX_ECUDA;
+  const uint64_t end = std::min(limit, bytes);
+  for (uint64_t o = A->up_end.empty() ? 0 : A->up_end.back(); o < end; o += kUploadPiece) {
+    const uint64_t n = std::min(kUploadPiece, bytes - o);
     cudaEvent_t ev = nullptr;
     if (cudaMemcpyAsync(A->d_payload.p + o, src + o, n, cudaMemcpyHostToDevice, A->up_st) != cudaSuccess ||
         cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
@@ -646,6 +658,12 @@ int start_payload_upload(aceapex_archive *A, const void *h_archive) {
     if (cudaEventRecord(ev, A->up_st) != cudaSuccess) return ACEAPEX_ECUDA;
   }
   return ACEAPEX_OK;
+}
+
+// the rest of the payload of a handle opened with defer_payload
+int start_payload_upload(aceapex_archive *A, const void *h_archive) {
+  return upload_pieces(A, static_cast<const uint8_t *>(h_archive) + A->h.off_payload, A->h.payload_bytes,
+                       ~uint64_t(0));
 }
 
 

@@ -457,7 +457,7 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
       const uint32_t rec = st.u32(4 * c);
       ll = rec & 0xFFFFu;
       ml = (rec >> 16) + mm;
-      src = st.le(offs + W * c, W);
+      src = W == 4 ? (uint64_t)st.u32(offs + 4 * c) : st.le(offs + W * c, W);  // (4-byte offsets are aligned)
     }
     const uint32_t inc_l = warp_incl_scan(ll, lane), inc_m = warp_incl_scan(ml, lane);
     const uint32_t lit_end = tot_l + inc_l, msum = tot_m + inc_m - ml;
@@ -570,7 +570,7 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
       const uint32_t rec = st.u32(4 * c);
       cum = rec >> 16;
       lend = rec & 0xFFFFu;
-      src = st.le(offs + W * c, W);
+      src = W == 4 ? (uint64_t)st.u32(offs + 4 * c) : st.le(offs + W * c, W);  // (4-byte offsets are aligned)
     }
     // match bytes of the commands before c (the previous lane's sum, or the
     // last sum of the previous chunk); this command's length is the difference
@@ -927,6 +927,11 @@ __global__ void __launch_bounds__(kDecodeThreads, 1) batch_kernel(DecodeLaunch L
     __syncthreads();  // the table is replaced only after every warp left this archive
   }
   PHASE_FLUSH();
+}
+
+__global__ void init_flags_kernel(uint64_t *flags, const SegRec *dir, uint64_t n) {
+  const uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (s < n) flags[s] = (uint64_t)dir[s].level << 32;
 }
 
 __global__ void begin_kernel(uint32_t *global_epoch, uint32_t *epoch, uint32_t *counter) {
@@ -1363,6 +1368,12 @@ cudaError_t launch_batch(const DecodeLaunch &L, uint32_t n_arcs, int grid, cudaS
   return cudaGetLastError();
 }
 
+cudaError_t launch_init_flags(uint64_t *flags, const SegRec *dir, uint64_t n, cudaStream_t st) {
+  if (!n) return cudaSuccess;
+  init_flags_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(flags, dir, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_begin(uint32_t *global_epoch, uint32_t *epoch, uint32_t *counter, cudaStream_t st) {
   begin_kernel<<<1, 1, 0, st>>>(global_epoch, epoch, counter);
   return cudaGetLastError();
@@ -1592,16 +1603,6 @@ __global__ void noalloc_setup_kernel(const uint8_t *tables) {
   }
 }
 
-// each segment's flag word: its directory level, no epoch (the level of a
-// corrupt record is caught by that segment's own checks, and a reader that
-// waits for it gives up once that segment latches the error)
-__global__ void noalloc_levels_kernel(const SegRec *dir, uint32_t n_seg) {
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < n_seg)
-    reinterpret_cast<uint64_t *>(g_noalloc_scratch + kNoAllocCtlBytes + kNoAllocLutBytes)[s] = (uint64_t)dir[s].level
-                                                                                                << 32;
-}
-
 // segments in index order (every source segment precedes its reader, so a
 // warp only waits for segments that running warps took earlier)
 __global__ void __launch_bounds__(256) noalloc_decode_kernel(DecodeLaunch L, uint64_t payload_bytes,
@@ -1723,7 +1724,9 @@ extern "C" int aceapex_decode_all_noalloc(const void *d_archive, uint64_t nbytes
   L.scratch_warps = kNoAllocWarps;
   L.wait_ns = 2000000000ull;
   noalloc_setup_kernel<<<1, 256, 0, st>>>(arc + kHeaderBytes);
-  noalloc_levels_kernel<<<(unsigned)((n_seg + 255) / 256), 256, 0, st>>>(A.dir, (uint32_t)n_seg);
+  // (a corrupt record's level is caught by that segment's own checks, and a
+  // reader that waits for it gives up once that segment latches the error)
+  launch_init_flags(A.flags, A.dir, n_seg, st);
   noalloc_decode_kernel<<<kNoAllocWarps / 8, 256, 0, st>>>(L, payload_bytes, h[30]);
   noalloc_status_kernel<<<1, 1, 0, st>>>(d_status);
   return cudaGetLastError() == cudaSuccess ? 0 : 4;

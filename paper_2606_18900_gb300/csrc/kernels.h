@@ -77,6 +77,10 @@ struct LaunchShape {
 // fresh epochs.
 cudaError_t launch_begin(uint32_t *global_epoch, uint32_t *epoch, uint32_t *counter, cudaStream_t st);
 
+// flags[s] = dir[s].level << 32 for s < n: each segment's flag word with its
+// level and no epoch
+cudaError_t launch_init_flags(uint64_t *flags, const SegRec *dir, uint64_t n, cudaStream_t st);
+
 // Persistent decode over L.work.
 cudaError_t launch_decode(const DecodeLaunch &L, int grid, int block, cudaStream_t st);
 
