@@ -682,22 +682,17 @@ int prepare_windows(aceapex_archive *a, uint64_t window, cudaStream_t st) {
   if (!a->copy_st && cudaStreamCreateWithFlags(&a->copy_st, cudaStreamNonBlocking) != cudaSuccess)
     return ACEAPEX_ECUDA;
   if (a->win_bytes != window) {
+    // (work made for another window size may still be queued)
     cudaStreamSynchronize(st);
-    std::vector<WorkItem> work;
-    std::vector<uint32_t> segs;
+    // window k is segments [k per, (k + 1) per), and its work list sits at
+    // the same place of the window lists, made on the device
+    const uint64_t per = window / S;
     a->win_start.clear();
-    for (uint64_t lo = 0; lo < a->h.n; lo += window) {
-      segs.clear();
-      const uint64_t s1 = std::min(a->h.n_seg, (lo + window) / S + ((lo + window) % S ? 1 : 0));
-      for (uint64_t s = lo / S; s < s1; ++s) segs.push_back((uint32_t)s);
-      a->win_start.push_back(work.size());
-      level_order(a->dir, segs.data(), segs.size(), 0, work);
-    }
-    a->win_start.push_back(work.size());
-    if (a->d_win_work.alloc(work.size()) != cudaSuccess ||
-        cudaMemcpy(a->d_win_work.p, work.data(), sizeof(WorkItem) * work.size(), cudaMemcpyHostToDevice) !=
-            cudaSuccess)
-      return ACEAPEX_ENOMEM;
+    for (uint64_t s = 0; s < a->h.n_seg; s += per) a->win_start.push_back(s);
+    a->win_start.push_back(a->h.n_seg);
+    if (a->d_win_work.alloc(std::max<uint64_t>(a->h.n_seg, 1)) != cudaSuccess) return ACEAPEX_ENOMEM;
+    if (launch_window_order(a->d_dir.p, a->h.n_seg, per, a->stats.max_level, a->d_win_work.p, st) != cudaSuccess)
+      return ACEAPEX_ECUDA;
     a->win_bytes = window;
   }
   const size_t nwin = a->win_start.size() - 1;

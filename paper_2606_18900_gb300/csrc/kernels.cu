@@ -518,13 +518,24 @@ __device__ __forceinline__ void decode_segment_impl(const DecodeLaunch &L, const
 #pragma unroll
         for (int u = 0; u < 4; ++u) p[32 * u] = (uint8_t)lit_rans();
       } else {
+        // the same walk as bound(), with the next run end kept relative to
+        // the block (D) and each lane's offset (ol) changed only at run ends,
+        // so that a step without one costs a compare and its store
+        int D = E - K0;
+        uint32_t ol = Sc + (uint32_t)lane;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const uint32_t o = bound();
+          uint32_t o = ol;
+          while (D < 32 * (u + 1)) {  // a run end inside step u, at lane D - 32 u
+            Sc = rec >> 16;
+            ol = Sc + (uint32_t)lane;
+            if (lane >= D - 32 * u) o = ol;
+            rec = st.u32(4 * ++cu);
+            E = (int)(rec & 0xFFFFu);
+            D = E - K0;
+          }
           outK[32 * u + o] = (uint8_t)lit_rans();
-          K0 += 32;
         }
-        K0 -= 128;
       }
       K0 += 128;
       outK += 128;
@@ -927,6 +938,28 @@ __global__ void __launch_bounds__(kDecodeThreads, 1) batch_kernel(DecodeLaunch L
     __syncthreads();  // the table is replaced only after every warp left this archive
   }
   PHASE_FLUSH();
+}
+
+// One warp per window of `per` segments: the window's segments in level
+// order, index order within a level (one pass over the window per level, a
+// ballot placing each pass's members), into out[s0 .. s1) of the window.
+__global__ void window_order_kernel(const SegRec *dir, uint64_t n_seg, uint64_t per, uint32_t max_level,
+                                    WorkItem *out) {
+  const uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t s0 = w * per;
+  if (s0 >= n_seg) return;  // (the whole warp)
+  const uint64_t s1 = min(n_seg, s0 + per);
+  const uint32_t lt = lanemask_lt();
+  uint64_t pos = s0;
+  for (uint32_t l = 0; l <= max_level; ++l)
+    for (uint64_t b = s0; b < s1; b += 32) {
+      const uint64_t s = b + lane;
+      const bool take = s < s1 && dir[s].level == l;
+      const uint32_t m = __ballot_sync(kFull, take);
+      if (take) out[pos + __popc(m & lt)] = WorkItem{0u, (uint32_t)s};
+      pos += __popc(m);
+    }
 }
 
 __global__ void init_flags_kernel(uint64_t *flags, const SegRec *dir, uint64_t n) {
@@ -1365,6 +1398,14 @@ cudaError_t launch_batch(const DecodeLaunch &L, uint32_t n_arcs, int grid, cudaS
   if (n_arcs == 0) return cudaSuccess;
   cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLutBytes);
   batch_kernel<<<grid, kDecodeThreads, kSmemLutBytes, st>>>(L, n_arcs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_window_order(const SegRec *dir, uint64_t n_seg, uint64_t per, uint32_t max_level, WorkItem *out,
+                                cudaStream_t st) {
+  if (!n_seg || !per) return cudaSuccess;
+  const uint64_t warps = (n_seg + per - 1) / per;
+  window_order_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(dir, n_seg, per, max_level, out);
   return cudaGetLastError();
 }
 

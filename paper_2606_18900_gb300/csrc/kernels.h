@@ -81,6 +81,11 @@ cudaError_t launch_begin(uint32_t *global_epoch, uint32_t *epoch, uint32_t *coun
 // level and no epoch
 cudaError_t launch_init_flags(uint64_t *flags, const SegRec *dir, uint64_t n, cudaStream_t st);
 
+// Work lists of windows of `per` segments: out[s0 .. s1) holds window
+// [s0, s1)'s segments by (level, index); max_level: the highest level present
+cudaError_t launch_window_order(const SegRec *dir, uint64_t n_seg, uint64_t per, uint32_t max_level, WorkItem *out,
+                                cudaStream_t st);
+
 // Persistent decode over L.work.
 cudaError_t launch_decode(const DecodeLaunch &L, int grid, int block, cudaStream_t st);
 
