@@ -259,6 +259,27 @@ def test_decode_all_to_host_windows(window):
             assert_same(host.numpy(), d)
 
 
+def test_decode_all_to_host_window_sizes_on_one_handle():
+    """One handle decodes to host memory with window sizes that change from
+    call to call (each change remakes the windows' work lists on the device),
+    ragged last windows included; every output equals the source, and a
+    whole-file decode on the device between them too."""
+    d = synth.pe_fastq((8 << 20) + 12345, ref_len=2_000_000)
+    a = ace.encode(d, min_match=12, max_level=5)
+    with ace.Archive(a) as arc:
+        s = torch.cuda.Stream()
+        for window in (1 << 20, 16384 * 5, 1 << 20, 0, 16384):
+            host = torch.zeros(d.size, dtype=torch.uint8).pin_memory()
+            arc.decode_all_to_host(host, window, s)
+            s.synchronize()
+            arc.check(s)
+            assert_same(host.numpy(), d)
+            out = torch.zeros(d.size, dtype=torch.uint8, device="cuda")
+            arc.decode_all(out, s)
+            arc.check(s)
+            assert_same(out.cpu().numpy(), d)
+
+
 @pytest.mark.parametrize("window", [0, 1 << 20, 16384])
 def test_decode_host_one_call(window):
     """aceapex_decode_host: host archive in, host output out, in one call,
