@@ -127,8 +127,9 @@ int aceapex_decode_all_to_host(aceapex_archive *a, void *h_out, uint64_t out_cap
  * the handle, returning when h_out[0..N) holds the output. The host checks
  * are aceapex_open's without the dependency lists and the read index, which
  * a whole-file decode does not read. Unlike open followed by a decode, the
- * payload goes to the device last, in 32 MiB pieces that decoding may
- * overtake: a window's decode starts once the pieces holding its segments
+ * payload goes to the device in 32 MiB pieces that decoding may overtake:
+ * the first two while the host checks run, the rest once the small sections
+ * are queued; a window's decode starts once the pieces holding its segments
  * have arrived, so the upload, the decodes and the copies back overlap.
  * h_archive (nbytes, caller-owned, read only; pinned
  * memory for the upload to overlap) is read until the call returns. Errors:
