@@ -440,7 +440,8 @@ int device_closure(aceapex_archive *A, uint64_t s_lo, uint64_t s_hi, cudaStream_
     if (cudaMemcpy(A->d_dep_ptr.p, A->dep_ptr.data(), 8 * (ns + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
         (A->h.n_deps &&
          cudaMemcpy(A->d_deps.p, A->deps.data(), 4 * A->h.n_deps, cudaMemcpyHostToDevice) != cudaSuccess) ||
-        cudaMemset(A->d_cmark.p, 0, 4 * ns) != cudaSuccess)
+        cudaMemset(A->d_cmark.p, 0, 4 * ns) != cudaSuccess ||
+        cudaStreamSynchronize(0) != cudaSuccess)  // (st need not wait for the legacy stream)
       return ACEAPEX_ECUDA;
     A->cgen = 0;
   }
@@ -938,7 +939,9 @@ int aceapex_last_error(aceapex_archive *a, int sync, void *stream) {
   if (e != cudaSuccess) return ACEAPEX_ECUDA;
   uint32_t v = 0;
   if (cudaMemcpy(&v, a->err(), 4, cudaMemcpyDeviceToHost) != cudaSuccess) return ACEAPEX_ECUDA;
-  if (v && cudaMemset(a->err(), 0, 4) != cudaSuccess) return ACEAPEX_ECUDA;
+  // (cleared on the legacy stream, which later non-blocking streams do not wait for)
+  if (v && (cudaMemset(a->err(), 0, 4) != cudaSuccess || cudaStreamSynchronize(0) != cudaSuccess))
+    return ACEAPEX_ECUDA;
   return v == 0 ? ACEAPEX_OK : (int)v;
 }
 
@@ -976,7 +979,9 @@ int aceapex_debug_block_segments(aceapex_archive *a, const uint32_t *segs, uint3
   if (cudaSetDevice(a->device) != cudaSuccess) return ACEAPEX_ECUDA;
   std::vector<uint8_t> b(std::max<uint64_t>(a->h.n_seg, 1), 0);
   for (uint32_t i = 0; i < n; ++i) b[segs[i]] = 1;
-  if (cudaMemcpy(a->d_blocked.p, b.data(), b.size(), cudaMemcpyHostToDevice) != cudaSuccess) return ACEAPEX_ECUDA;
+  if (cudaMemcpy(a->d_blocked.p, b.data(), b.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaStreamSynchronize(0) != cudaSuccess)
+    return ACEAPEX_ECUDA;
   a->any_blocked = n != 0;
   return ACEAPEX_OK;
 }

@@ -342,6 +342,12 @@ int aceapex_server_create(aceapex_archive *const *as, int n, uint64_t mem_budget
       return ACEAPEX_ENOMEM;
     }
   }
+  // the page-table fills and flag copies above ran on the legacy stream,
+  // which the slots' non-blocking streams do not wait for
+  if (cudaStreamSynchronize(0) != cudaSuccess) {
+    aceapex_server_destroy(S);
+    return ACEAPEX_ECUDA;
+  }
   S->worker = std::thread(worker_loop, S);
   const unsigned hw = std::thread::hardware_concurrency();
   const unsigned nw = std::max(1u, std::min(8u, hw / 2));
